@@ -1,0 +1,327 @@
+"""Benchmark: spaND factor + s-step GMRES solve of the DG Newton-step system.
+
+Workload (default): p=2 modal DG Jacobian of 2D Euler on a seeded 64 x 32
+NACA O-grid (K=2048, N=73,728), eps=1e-3, s=4, restart 60, tol 1e-8.  One
+step = spand_factor + sstep_gmres_solve to a true FP64 relative residual
+<= 1e-8, inputs resident in HBM.  The headline form is the mixed one (FP32 /
+TF32 factor and apply, FP64 SpMV / Gram / CholQR / Hessenberg); the FP64 form
+is timed beside it for the speedup.  The L2 is flushed between timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the CPU oracle (NumPy/SciPy) on the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "spaND factor+s-step GMRES time to 1e-8 rel residual; mixed vs FP64 speedup"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300")
+    ap.add_argument("--config", default="C2")
+    return ap.parse_args()
+
+
+def workload(cname):
+    from synth import get_config, modal_state, naca_ogrid
+    c = get_config(cname)
+    X = naca_ogrid(c.n_theta, c.n_r, c.seed)
+    u = modal_state(X, c.p, c.mach, c.alpha_deg, c.amp, c.seed)
+    return c, X, u
+
+
+def config_json(c, extra=None):
+    d = {"workload": f"DG Euler Jacobian p={c.p} O-grid {c.n_theta}x{c.n_r} (K={c.K}, N={c.N}), "
+                     f"spaND eps={c.eps}, s-step GMRES s={c.s} restart={c.restart} tol={c.tol}",
+         "N": c.N, "block": c.B, "eps": c.eps, "s": c.s, "restart": c.restart, "tol": c.tol,
+         "l2": "flushed between timed steps (256 MB write)"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, idx=0):
+        self.idx = idx
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for n, v in zip(names, s[4:8]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            return d, "measured"
+        except Exception:
+            pass
+    return dict(PEAKS_FALLBACK), "fallback"
+
+
+def run_reference(args):
+    """CPU oracle arm: full factor + s-step GMRES solves of the same workload."""
+    import numpy as np
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import dg, spand
+    from oracle.gmres import sstep_gmres
+    c, X, u = workload(args.config)
+    rhs, bsr, _ = dg.assemble(X, c.p, u, c.mach, c.alpha_deg, c.cfl)
+    A = dg.bsr_to_scipy(*bsr).tocsr()
+    times = []
+    budget = 180.0
+    t_all = time.time()
+    for k in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        F = spand.factor(bsr, c.n_theta, c.n_r, c.nd_depth, c.eps)
+        x, st = sstep_gmres(lambda v: A @ v, lambda v: spand.apply(F, v), rhs, s=c.s, restart=c.restart,
+                            tol=c.tol, max_iters=c.max_iters)
+        times.append(time.perf_counter() - t0)
+        if time.time() - t_all > budget:
+            break
+    ms = 1e3 * statistics.mean(times)
+    cores = os.cpu_count()
+    out = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus, "steps": len(times),
+           "warmup": 0, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": config_json(c),
+           "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle",
+                            "sample": f"{len(times)} full factor+solve(s) of the workload (oracle as it stands)"},
+           "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "true_relres": float(st.true_relres), "iters": st.iters}
+    print(json.dumps(out))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__ as g
+    g.build()
+    import paper_2101_01763_gb300 as sg
+    c, X, u = workload(args.config)
+    stream = torch.cuda.current_stream()
+    Xd = torch.as_tensor(X, device=dev)
+    ud = torch.as_tensor(u, device=dev)
+    rhs, A, dtau = sg.assemble(Xd, c.p, ud, c.mach, c.alpha_deg, c.cfl)
+    plan = sg.Plan(c.n_theta, c.n_r, c.B, c.nd_depth)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def one(prec):
+        F = sg.Factor(plan, A, c.eps, prec)
+        x, st = sg.sstep_gmres(A, F, rhs, s=c.s, restart=c.restart, tol=c.tol, max_iters=c.max_iters)
+        return F, x, st
+
+    def timed(prec, steps, warmup):
+        for _ in range(warmup):
+            F, x, st = one(prec)
+            F.close()
+        ev = []
+        stats = None
+        barrier()
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            F = sg.Factor(plan, A, c.eps, prec)
+            e1.record(stream)
+            x, st = sg.sstep_gmres(A, F, rhs, s=c.s, restart=c.restart, tol=c.tol, max_iters=c.max_iters)
+            e2.record(stream)
+            torch.cuda.synchronize()
+            ev.append((e0.elapsed_time(e1), e1.elapsed_time(e2)))
+            stats = (F.stats(), st, x)
+            F.close()
+        barrier()
+        return ev, stats
+
+    # ---- headline: mixed form
+    with Clocks(local) as clk:
+        ev_mx, (fst_mx, gst_mx, x_mx) = timed("mixed", args.steps, args.warmup)
+    # ---- FP64 form beside it (fewer steps: its factorization is FP64-ALU bound)
+    k64 = max(2, min(args.steps, 4))
+    ev_64, (fst_64, gst_64, x_64) = timed("fp64", k64, max(1, min(args.warmup, 2)))
+    t_mx = statistics.mean(a + b for a, b in ev_mx)
+    t_64 = statistics.mean(a + b for a, b in ev_64)
+    # true residual of the final mixed solution (independent FP64 SpMV)
+    r = sg.spmv(A, x_mx)
+    relres = (torch.linalg.norm(r - rhs) / torch.linalg.norm(rhs)).item()
+
+    # ---- roofline of the preconditioner apply (HBM-bound GEMV sweeps), timed live
+    F = sg.Factor(plan, A, c.eps, "mixed")
+    z = torch.empty_like(rhs)
+    for _ in range(3):
+        F.apply(rhs, out=z)
+    napp = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(napp):
+        F.apply(rhs, out=z)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_apply = e0.elapsed_time(e1) / napp
+    fb = F.stats()["factor_bytes"]
+    F.close()
+    pk, pk_kind = peaks()
+    hbm = float(pk.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    achieved = fb / (t_apply * 1e-3) / 1e9
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies inside
+    h_val = A.val.cpu().pin_memory()
+    h_rp = A.row_ptr.cpu().pin_memory()
+    h_col = A.col.cpu().pin_memory()
+    h_b = rhs.cpu().pin_memory()
+    h_x = torch.empty_like(h_b).pin_memory()
+    d_val = torch.empty_like(A.val)
+    d_rp = torch.empty_like(A.row_ptr)
+    d_col = torch.empty_like(A.col)
+    d_b = torch.empty_like(rhs)
+    A2 = sg.BSR(A.K, A.B, d_rp, d_col, d_val)
+    e2e = []
+    for it in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d_val.copy_(h_val, non_blocking=True)
+        d_rp.copy_(h_rp, non_blocking=True)
+        d_col.copy_(h_col, non_blocking=True)
+        d_b.copy_(h_b, non_blocking=True)
+        F2 = sg.Factor(plan, A2, c.eps, "mixed")
+        x2, _ = sg.sstep_gmres(A2, F2, d_b, s=c.s, restart=c.restart, tol=c.tol, max_iters=c.max_iters)
+        h_x.copy_(x2, non_blocking=True)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            e2e.append(time.perf_counter() - t0)
+        F2.close()
+    bi = h_val.numel() * 8 + h_rp.numel() * 4 + h_col.numel() * 4 + h_b.numel() * 8
+    bo = h_x.numel() * 8
+
+    # ---- max over ranks
+    vals = torch.tensor([t_mx, t_64, 1e3 * statistics.mean(e2e)], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
+    t_mx, t_64, t_e2e = vals.tolist()
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    # ---- CPU baseline: the oracle on a bounded sample (one full factor+solve)
+    cpu = None
+    if world == 1 and os.environ.get("BENCH_SKIP_CPU", "0") != "1":
+        from oracle import dg, spand
+        from oracle.gmres import sstep_gmres
+        rhs_o, bsr, _ = dg.assemble(X, c.p, u, c.mach, c.alpha_deg, c.cfl)
+        So = dg.bsr_to_scipy(*bsr).tocsr()
+        t0 = time.perf_counter()
+        Fo = spand.factor(bsr, c.n_theta, c.n_r, c.nd_depth, c.eps)
+        xo, so = sstep_gmres(lambda v: So @ v, lambda v: spand.apply(Fo, v), rhs_o, s=c.s, restart=c.restart,
+                             tol=c.tol, max_iters=c.max_iters)
+        tcpu = time.perf_counter() - t0
+        err = float(np.linalg.norm(x_mx.cpu().numpy() - xo) / np.linalg.norm(xo))
+        cpu = {"value": 1e3 * tcpu, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "one full factor+solve of the workload (NumPy/SciPy FP64, multithreaded BLAS)",
+               "mixed_solution_rel_err_vs_oracle": err}
+    out = {
+        "metric": METRIC, "value": t_mx, "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_mx, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": config_json(c, {"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                                  "form": "mixed (FP32/TF32 factor+apply, FP64 outer)"}),
+        "fp64_ms_per_step": t_64, "speedup_mixed_vs_fp64": t_64 / t_mx,
+        "factor_ms": statistics.mean(a for a, _ in ev_mx), "solve_ms": statistics.mean(b for _, b in ev_mx),
+        "fp64_factor_ms": statistics.mean(a for a, _ in ev_64), "fp64_solve_ms": statistics.mean(b for _, b in ev_64),
+        "gmres_iters_mixed": gst_mx["iters"], "gmres_iters_fp64": gst_64["iters"],
+        "true_relres_mixed": relres, "ranks_per_level": fst_mx["sum_r"],
+        "solves_per_s": world * 1e3 / t_mx,
+        "e2e": {"value": t_e2e, "unit": "ms", "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
+        "gpu_launches": None,
+        "roofline": {"kernel": "spand_apply (gather-GEMV sweeps, FP32 factors)", "bound": "hbm",
+                     "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": None, "peak_kind": pk_kind, "bytes_per_launch": fb, "ms_per_launch": t_apply},
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

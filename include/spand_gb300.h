@@ -1,0 +1,207 @@
+/*
+ * spand_gb300.h - C ABI of the GB300 (sm_103a) spaND + s-step GMRES library.
+ *
+ * Hot path of the implicit DG solver of arXiv 2101.01763: the linear solve of
+ * one pseudo-time Newton step (Sec. 2.1.2, Eq. 5)
+ *        (M/dtau + dR/du) du = -R,
+ * by sparsified nested dissection (spaND, Sec. 2.2.1) used as a preconditioner
+ * for s-step GMRES (Sec. 2.3, Algorithm 2).
+ *
+ * Conventions shared by every entry point
+ *  - Return value: int status; 0 = SPAND_OK, negative = error (codes below).
+ *    On error no output is guaranteed; handles stay valid and must still be
+ *    destroyed.  No entry point writes host globals.
+ *  - Pointers documented as "device" must point to device memory owned by the
+ *    caller (any allocator); "host" pointers are caller-owned host memory.
+ *    Handles (spand_plan_t, spand_factor_t) are owned by the library and are
+ *    released by the matching *_destroy.
+ *  - Block-CSR (BSR) matrices: K block rows of size B = 4 (p+1)^2, 0-based
+ *    int32 row_ptr[K+1] / col[nnzb] with ascending columns in a row, values
+ *    val[nnzb * B * B] with block k stored column-major:
+ *    element (r, c) of block k at val[k*B*B + c*B + r].
+ *  - DOF numbering: element e (e = i*n_theta + j, i radial, j angular), mode
+ *    m = b*(p+1) + a (degree a in xi, b in eta), variable v in
+ *    (rho, rho u, rho v, E): global index e*B + m*4 + v.
+ *  - Work is enqueued on the given stream; entry points that must read a
+ *    device result (ranks in spand_factor, residual estimates in the GMRES
+ *    loop, dtau) synchronize that stream before returning.
+ */
+#ifndef SPAND_GB300_H
+#define SPAND_GB300_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  SPAND_OK = 0,
+  SPAND_ERR_ARG = -1,            /* invalid argument (null pointer, bad size)        */
+  SPAND_ERR_NOMEM = -2,          /* device or host allocation failed                 */
+  SPAND_ERR_ZERO_PIVOT = -3,     /* exact zero pivot in a block LU                    */
+  SPAND_ERR_CHOLQR = -4,         /* CholQR Gram matrix not positive definite          */
+  SPAND_ERR_NONFINITE = -5,      /* NaN/Inf met in a residual or a factor             */
+  SPAND_ERR_NOT_CONVERGED = -6,  /* GMRES reached max_iters above tolerance           */
+  SPAND_ERR_CUDA = -7,           /* a CUDA runtime call failed                        */
+  SPAND_ERR_UNSUPPORTED = -8     /* configuration outside the supported range         */
+};
+
+enum { SPAND_BC_WALL = 0, SPAND_BC_FARFIELD = 1 };
+enum { SPAND_FP64 = 0, SPAND_MIXED = 1 };
+enum { SPAND_BASIS_NEWTON = 0, SPAND_BASIS_MONOMIAL = 1 };
+
+/* Structured O-grid: nodes[(i*n_theta + j)*2 + {0,1}] = (x, y) of node (i, j),
+ * i = 0..n_r (0 = airfoil), j = 0..n_theta-1 (periodic, clockwise).  Device. */
+typedef struct {
+  int n_theta;
+  int n_r;
+  const double* nodes;
+} dg_mesh;
+
+typedef struct {
+  double gamma;      /* ratio of specific heats                                   */
+  double mach;       /* free-stream Mach number (rho_inf = 1, p_inf = 1/gamma)     */
+  double alpha_deg;  /* angle of attack in degrees                                 */
+  double cfl;        /* CFL number of Eq. 8                                        */
+  int bc_mode;       /* SPAND_BC_WALL (slip wall on the airfoil) or SPAND_BC_FARFIELD */
+} dg_flow_params;
+
+/* Device BSR matrix (see conventions above).  For dg_assemble_jacobian the
+ * caller allocates row_ptr (K+1), col (nnzb = 5K - 2 n_theta) and val
+ * (nnzb*B*B) and the library fills all three. */
+typedef struct {
+  int K;
+  int B;
+  int nnzb;
+  int* row_ptr;
+  int* col;
+  double* val;
+} bsr_matrix;
+
+/* ---------------------------------------------------------------- assembly
+ * dg_assemble_jacobian - Sec. 2.1.2 (Eqs. 3-8): modal DG discretisation of 2D
+ * Euler (tensor orthonormal Legendre basis of degree p in 1..3, Gauss-Legendre
+ * quadrature with p+2 points per direction, Rusanov flux), returning
+ *     rhs = -R(u_hat)                       (device, N = K*B doubles)
+ *     A   = M/dtau + dR/du (exact derivative; block-CSR, device)
+ *     *dtau_out = min_k CFL/lambda_k        (host double)
+ * with lambda_k = max over the element's quadrature points of (|v| + c)
+ * times (2p+1) |dD_k| / |D_k|.  u_hat is device [K, (p+1)^2, 4] doubles.
+ * Errors: SPAND_ERR_ARG, SPAND_ERR_UNSUPPORTED (p outside 1..3, n_theta < 4),
+ * SPAND_ERR_NONFINITE (non-physical state), SPAND_ERR_CUDA.               */
+int dg_assemble_jacobian(const dg_mesh* mesh, int p, const double* u_hat,
+                         const dg_flow_params* flow, double* rhs, bsr_matrix* A,
+                         double* dtau_out, cudaStream_t stream);
+
+/* y = A x (transpose = 0) or y = A^T x (transpose = 1); FP64, device vectors
+ * of length K*B.  The block-SpMV of Algorithm 2's matrix-powers step. */
+int bsr_spmv(const bsr_matrix* A, const double* x, double* y, int transpose,
+             cudaStream_t stream);
+
+/* ---------------------------------------------------------------- analysis
+ * spand_analyze - Sec. 2.2.1 and Sec. 3.3: nested dissection of the
+ * n_theta x n_r element grid (root separator = radial lines j = 0 and
+ * j = n_theta/2; then recursive bisection across the longer extent, ties
+ * along j, at lo + (n-1)/2; leaves at depth D or extent < 3), the interiors,
+ * interfaces and merges of every level 0..D, and the block pattern with
+ * fill-in.  Pattern-only (integer) work on the host; reusable for every
+ * factorization of matrices on the same grid.  depth_D <= 0 selects
+ * D = max(1, ceil(log2(K/32))).  Errors: SPAND_ERR_ARG, SPAND_ERR_NOMEM. */
+typedef struct spand_plan_s* spand_plan_t;
+int spand_analyze(int n_theta, int n_r, int B, int depth_D, spand_plan_t* out);
+int spand_plan_destroy(spand_plan_t plan);
+
+/* Plan tables, for checking against an independent implementation.  Host
+ * buffers.  spand_plan_sizes: K, D, number of tree nodes and the length of
+ * the serialized cluster table.  spand_plan_export writes owner[K] (tree node
+ * owning each element, nodes in preorder), node_level[n_nodes] and the
+ * cluster table: for each level l = 0..D: n_clusters, then per cluster
+ * node, interior, n_key, key[n_key], n_elems, elems[n_elems], n_children,
+ * children[n_children] (n_children = 0 at level 0). */
+int spand_plan_sizes(spand_plan_t plan, int* K, int* D, int* n_nodes, int64_t* table_len);
+int spand_plan_export(spand_plan_t plan, int* owner, int* node_level, int* table);
+
+/* ---------------------------------------------------------------- factor
+ * spand_factor - Sec. 2.2.1 (Eqs. 9-11), level by level: eliminate interiors
+ * by row-pivoted block LU with Schur updates; scale every interface by its
+ * own PLU with diag(U) split evenly (L~ = L|D|^1/2, U~ = |D|^-1/2 U); compute
+ * every interface's column-pivoted Householder QR of [A_sn A_ns^T], keep the
+ * rank r = #{k : |R_kk| > eps |R_00|}, compress every block to
+ * Q_ic^T A_ij Q_jc and merge.  eps = 0 gives an exact direct factorization.
+ * precision: SPAND_FP64 (all factor arithmetic in FP64) or SPAND_MIXED
+ * (factors computed and stored in FP32; the FP32 GEMMs of the Schur,
+ * scaling and compression updates use TF32 tensor cores with FP32
+ * accumulation).  A is read only; the factor owns its device memory.
+ * Errors: SPAND_ERR_ARG, SPAND_ERR_NOMEM, SPAND_ERR_ZERO_PIVOT,
+ * SPAND_ERR_NONFINITE, SPAND_ERR_CUDA. */
+typedef struct spand_factor_s* spand_factor_t;
+int spand_factor(spand_plan_t plan, const bsr_matrix* A, double eps, int precision,
+                 spand_factor_t* out, cudaStream_t stream);
+int spand_factor_destroy(spand_factor_t F);
+
+typedef struct {
+  int levels;               /* D + 1                                          */
+  int64_t n_sparsified[32]; /* interfaces sparsified at level l               */
+  int64_t sum_n[32];        /* sum of their sizes before sparsification      */
+  int64_t sum_r[32];        /* sum of kept ranks                              */
+  int64_t max_r[32];        /* largest kept rank                              */
+  int64_t top_size;         /* size of the last (root) interior               */
+  int64_t factor_bytes;     /* device bytes one spand_apply streams (both sweeps) */
+  double factor_flops;      /* algorithmic flops of the factorization         */
+} spand_stats;
+int spand_factor_stats(spand_factor_t F, spand_stats* st);
+
+/* ---------------------------------------------------------------- apply
+ * spand_apply - z = M^-1 r (transpose = 0) or z = M^-T r (transpose = 1) for
+ * the preconditioner M = prod F_i of Sec. 2.2.1: the forward sweep applies the
+ * elimination, scaling and orthogonal operators level by level, the backward
+ * sweep their counterparts in reverse; the transpose runs the transposed
+ * operators in the opposite order.  r, z: device FP64 vectors of length N
+ * (may not alias).  In SPAND_MIXED the sweep runs in FP32.  Not reentrant on
+ * one factor: calls on one factor must be ordered (same stream). */
+int spand_apply(spand_factor_t F, const double* r, double* z, int transpose,
+                cudaStream_t stream);
+
+/* ---------------------------------------------------------------- GMRES
+ * sstep_gmres_solve - Algorithm 2: s-step GMRES with right preconditioning
+ * (A M^-1 u = b, x = x0 + M^-1 Q y), Newton basis (shifts = Ritz values of s
+ * classical GMRES steps of the first cycle, real Leja order) or monomial
+ * basis, one Gram reduction per s-block with the lagged second CGS + CholQR
+ * pass, Givens least squares, restart after `restart` basis vectors.
+ * Converged when the true FP64 residual ||b - A x|| / ||b|| <= tol at a
+ * restart.  M may be NULL (no preconditioner).  x: device, in = x0,
+ * out = solution.  transpose = 1 solves A^T x = b with M^-T.
+ * Errors: SPAND_ERR_ARG, SPAND_ERR_CHOLQR, SPAND_ERR_NONFINITE,
+ * SPAND_ERR_NOT_CONVERGED (x holds the last iterate), SPAND_ERR_CUDA. */
+typedef struct {
+  int s;            /* block size (1..16)                          */
+  int restart;      /* basis vectors per cycle, multiple of s      */
+  double tol;       /* relative residual target                    */
+  int max_iters;    /* cap on Hessenberg columns over all cycles   */
+  int basis;        /* SPAND_BASIS_NEWTON / SPAND_BASIS_MONOMIAL   */
+  int transpose;    /* 0: A x = b; 1: A^T x = b                    */
+} gmres_opts;
+
+typedef struct {
+  int iters;            /* Hessenberg columns used                        */
+  int restarts;         /* completed cycles                               */
+  int reductions;       /* Gram reductions                                */
+  double true_relres;   /* final ||b - A x|| / ||b|| (FP64)               */
+  double est_relres;    /* last Givens estimate                           */
+  double orth_err;      /* max over cycles of ||Q^T Q - I||_F             */
+  double shifts_re[16]; /* Newton shifts in Leja order                    */
+  double shifts_im[16];
+  double t_spmv_ms, t_apply_ms, t_orth_ms, t_small_ms; /* phase times (events) */
+} gmres_stats;
+
+int sstep_gmres_solve(const bsr_matrix* A, spand_factor_t M, const double* b, double* x,
+                      const gmres_opts* opts, gmres_stats* stats, cudaStream_t stream);
+
+const char* spand_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPAND_GB300_H */

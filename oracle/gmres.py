@@ -203,8 +203,9 @@ def sstep_gmres(Aop, Mop, b, x0=None, s=4, restart=40, tol=1e-8, max_iters=400,
         c = 0                                  # last final column
         pend = None                            # (P, R1, S1, t0, c_start)
         done = False
-        if first_cycle and basis == "newton" and shifts is None:
-            # s classical GMRES steps supply the Ritz values and H[:, :s]
+        if basis == "newton" and shifts is None:
+            # s classical GMRES steps supply the Ritz values and H[:, :s] (the first
+            # cycle that runs them to completion fixes the shifts for later cycles)
             for j in range(s):
                 v = Aop(Mop(Qf[:, j]))
                 for i in range(j + 1):
@@ -221,10 +222,10 @@ def sstep_gmres(Aop, Mop, b, x0=None, s=4, restart=40, tol=1e-8, max_iters=400,
                     break
             if not done:
                 shifts = leja_order(np.linalg.eigvals(H[:s, :s]))
-        if shifts is None:
-            shifts = [0j] * s
+        if shifts is None and not done:
+            shifts = [0j] * s                  # monomial basis
         st.shifts = shifts
-        Bm = change_of_basis(shifts)
+        Bm = change_of_basis(shifts) if shifts is not None else None
         first_cycle = False
 
         def finalize(pend, c, G_P, XP):

@@ -1,0 +1,190 @@
+"""Thin Python layer over the C ABI.  PyTorch provides device memory and
+streams; every computation runs in the library's CUDA kernels."""
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _need(t, dtype, name):
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+
+
+class BSR:
+    """Device block-CSR matrix (blocks column-major, see the C header)."""
+
+    def __init__(self, K, B, row_ptr, col, val):
+        self.K, self.B = K, B
+        self.row_ptr, self.col, self.val = row_ptr, col, val
+        self.nnzb = col.numel()
+
+    def struct(self):
+        return L.BsrMatrix(self.K, self.B, self.nnzb, self.row_ptr.data_ptr(), self.col.data_ptr(),
+                           self.val.data_ptr())
+
+    @staticmethod
+    def empty(K, B, nnzb, device="cuda"):
+        return BSR(K, B, torch.empty(K + 1, dtype=torch.int32, device=device),
+                   torch.empty(nnzb, dtype=torch.int32, device=device),
+                   torch.empty(nnzb * B * B, dtype=torch.float64, device=device))
+
+    @staticmethod
+    def from_host(row_ptr, col, val_rowmajor, device="cuda"):
+        """From (row_ptr, col, val[nnzb, B, B] row-major blocks) numpy arrays."""
+        nnzb, B, _ = val_rowmajor.shape
+        v = np.ascontiguousarray(np.transpose(val_rowmajor, (0, 2, 1))).reshape(-1)
+        return BSR(len(row_ptr) - 1, B, torch.as_tensor(np.asarray(row_ptr, np.int32), device=device),
+                   torch.as_tensor(np.asarray(col, np.int32), device=device),
+                   torch.as_tensor(v, dtype=torch.float64, device=device))
+
+    def blocks_rowmajor(self):
+        """val as a host [nnzb, B, B] row-major array."""
+        v = self.val.detach().cpu().numpy().reshape(self.nnzb, self.B, self.B)
+        return np.transpose(v, (0, 2, 1))
+
+
+def assemble(nodes, p, u_hat, mach, alpha_deg, cfl, gamma=1.4, bc="wall", stream=None):
+    """dg_assemble_jacobian: returns (rhs, A, dtau).  nodes: cuda f64 [n_r+1, n_theta, 2]."""
+    _need(nodes, torch.float64, "nodes")
+    _need(u_hat, torch.float64, "u_hat")
+    n_r, n_theta = nodes.shape[0] - 1, nodes.shape[1]
+    K = n_r * n_theta
+    B = 4 * (p + 1) ** 2
+    nnzb = 5 * K - 2 * n_theta if n_r > 1 else 3 * K
+    A = BSR.empty(K, B, nnzb, device=nodes.device)
+    rhs = torch.empty(K * B, dtype=torch.float64, device=nodes.device)
+    mesh = L.DgMesh(n_theta, n_r, nodes.data_ptr())
+    flow = L.DgFlow(gamma, mach, alpha_deg, cfl, L.BC_WALL if bc == "wall" else L.BC_FARFIELD)
+    Ast = A.struct()
+    dt = C.c_double(0.0)
+    L.check(L.lib().dg_assemble_jacobian(C.byref(mesh), p, _ptr(u_hat), C.byref(flow), _ptr(rhs),
+                                         C.byref(Ast), C.byref(dt), _stream(stream)), "dg_assemble_jacobian")
+    A.nnzb = Ast.nnzb
+    return rhs, A, dt.value
+
+
+def spmv(A, x, transpose=False, out=None, stream=None):
+    _need(x, torch.float64, "x")
+    y = torch.empty_like(x) if out is None else out
+    st = A.struct()
+    L.check(L.lib().bsr_spmv(C.byref(st), _ptr(x), _ptr(y), int(transpose), _stream(stream)), "bsr_spmv")
+    return y
+
+
+class Plan:
+    """spand_analyze: nested-dissection plan of an n_theta x n_r grid."""
+
+    def __init__(self, n_theta, n_r, B, depth=0):
+        h = C.c_void_p()
+        L.check(L.lib().spand_analyze(n_theta, n_r, B, depth, C.byref(h)), "spand_analyze")
+        self.h = h
+        self.n_theta, self.n_r, self.B = n_theta, n_r, B
+
+    def export(self):
+        K, D, nn, tl = C.c_int(), C.c_int(), C.c_int(), C.c_int64()
+        L.check(L.lib().spand_plan_sizes(self.h, C.byref(K), C.byref(D), C.byref(nn), C.byref(tl)), "sizes")
+        owner = np.zeros(K.value, np.int32)
+        lev = np.zeros(nn.value, np.int32)
+        tab = np.zeros(tl.value, np.int32)
+        L.check(L.lib().spand_plan_export(self.h, owner.ctypes.data_as(C.c_void_p),
+                                          lev.ctypes.data_as(C.c_void_p), tab.ctypes.data_as(C.c_void_p)),
+                "export")
+        return dict(K=K.value, D=D.value, owner=owner, node_level=lev, table=tab)
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                L.lib().spand_plan_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+
+def parse_table(table, D):
+    """Cluster table of spand_plan_export -> list over levels of cluster dicts."""
+    levels, k = [], 0
+    for _ in range(D + 1):
+        nc = int(table[k]); k += 1
+        cl = []
+        for _ in range(nc):
+            node, inter = int(table[k]), bool(table[k + 1]); k += 2
+            nk = int(table[k]); k += 1
+            key = [int(v) for v in table[k:k + nk]]; k += nk
+            ne = int(table[k]); k += 1
+            el = [int(v) for v in table[k:k + ne]]; k += ne
+            nch = int(table[k]); k += 1
+            ch = [int(v) for v in table[k:k + nch]]; k += nch
+            cl.append(dict(node=node, interior=inter, key=key, elems=el, children=ch))
+        levels.append(cl)
+    return levels
+
+
+class Factor:
+    """spand_factor: spaND preconditioner of A with tolerance eps."""
+
+    def __init__(self, plan, A, eps, precision="fp64", stream=None):
+        prec = L.SPAND_FP64 if precision == "fp64" else L.SPAND_MIXED
+        h = C.c_void_p()
+        st = A.struct()
+        L.check(L.lib().spand_factor(plan.h, C.byref(st), float(eps), prec, C.byref(h), _stream(stream)),
+                "spand_factor")
+        self.h = h
+        self.N = A.K * A.B
+        self.precision = precision
+
+    def apply(self, r, transpose=False, out=None, stream=None):
+        _need(r, torch.float64, "r")
+        z = torch.empty_like(r) if out is None else out
+        L.check(L.lib().spand_apply(self.h, _ptr(r), _ptr(z), int(transpose), _stream(stream)), "spand_apply")
+        return z
+
+    def stats(self):
+        s = L.SpandStats()
+        L.check(L.lib().spand_factor_stats(self.h, C.byref(s)), "spand_factor_stats")
+        n = s.levels
+        return dict(levels=n, n_sparsified=list(s.n_sparsified[:n]), sum_n=list(s.sum_n[:n]),
+                    sum_r=list(s.sum_r[:n]), max_r=list(s.max_r[:n]), top_size=s.top_size,
+                    factor_bytes=s.factor_bytes, factor_flops=s.factor_flops)
+
+    def close(self):
+        if getattr(self, "h", None):
+            L.lib().spand_factor_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sstep_gmres(A, M, b, x0=None, s=4, restart=40, tol=1e-8, max_iters=400, basis="newton",
+                transpose=False, stream=None, raise_on_nonconvergence=False):
+    """sstep_gmres_solve: returns (x, stats dict)."""
+    _need(b, torch.float64, "b")
+    x = torch.zeros_like(b) if x0 is None else x0.clone()
+    opts = L.GmresOpts(s, restart, tol, max_iters, L.BASIS_NEWTON if basis == "newton" else L.BASIS_MONOMIAL,
+                       int(transpose))
+    stt = L.GmresStats()
+    st = A.struct()
+    status = L.lib().sstep_gmres_solve(C.byref(st), M.h if M is not None else None, _ptr(b), _ptr(x),
+                                       C.byref(opts), C.byref(stt), _stream(stream))
+    if status != L.OK and (status != -6 or raise_on_nonconvergence):
+        L.check(status, "sstep_gmres_solve")
+    stats = dict(iters=stt.iters, restarts=stt.restarts, reductions=stt.reductions,
+                 true_relres=stt.true_relres, est_relres=stt.est_relres, orth_err=stt.orth_err,
+                 shifts=[complex(stt.shifts_re[k], stt.shifts_im[k]) for k in range(s)],
+                 converged=(status == L.OK))
+    return x, stats

@@ -1,0 +1,644 @@
+// Batched dense kernels on variable-size column-major matrices (FP64 / FP32).
+//
+// These carry the per-level block operations of spaND (Sec. 2.2.1):
+//   * getrf: right-looking blocked LU with partial pivoting (Eq. 9, Eq. 10);
+//     one launch per 32-column panel (one CTA per matrix) followed by a
+//     grouped GEMM for the trailing update;
+//   * grouped GEMM: C = beta C + alpha sum_t op(A_t) op(B_t), one CTA per
+//     64x64 output tile, all terms of a target accumulated by that CTA
+//     (Schur updates of Eq. 9 without atomics);
+//   * triangular inverses: L^-1 P^T and U^-1 (optionally with the scaling
+//     split of Eq. 10), one CTA per 32-column tile;
+//   * column-pivoted Householder QR truncated at |R_kk| <= eps |R_00| (the
+//     rank-revealing QR of Eq. 11) and the explicit Q_c it defines;
+//   * block copies / transposed copies / identity fills for gathers and merges.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace spand {
+
+constexpr int LU_NB = 32;
+
+template <typename T>
+struct MatRef {      // square matrix for getrf / inverses
+  T* A;
+  int n;
+  int* ipiv;         // n pivots (absolute 0-based rows)
+  int* perm;         // n: (P^T b)[k] = b[perm[k]]
+};
+
+template <typename T>
+struct GemmTask {
+  T* C;
+  int ldc, m, n;
+  T alpha, beta;
+  int t0, t1;        // term range
+};
+
+template <typename T>
+struct GemmTerm {
+  const T* A;
+  const T* B;
+  int lda, ldb, k, ta, tb;
+};
+
+struct TileItem {
+  int task, tm, tn;
+};
+
+template <typename T>
+struct CopyTask {    // dst[r + c*ldd] = scale * (trans ? src[c + r*lds] : src[r + c*lds])
+  const T* src;
+  T* dst;
+  int lds, ldd, rows, cols, trans;
+};
+
+struct CopyTile {
+  int task, tr, tc;
+};
+
+template <typename T>
+struct QrTask {
+  T* W;              // n x c column-major, ld = n; reflectors stored below the diagonal
+  T* tau;            // min(n, c)
+  T* norm2;          // c scratch
+  T* Q;              // explicit Q_c output (n x r, ld = n)
+  int n, c;
+  int* rank;         // output
+};
+
+// ------------------------------------------------------------------ reductions
+template <typename T>
+__device__ inline void argmax_pair(T& v, int& i, T v2, int i2) {
+  if (v2 > v || (v2 == v && i2 < i)) {
+    v = v2;
+    i = i2;
+  }
+}
+
+template <typename T>
+__device__ inline void block_argmax(T& v, int& idx, T* sv, int* si) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) {
+    T v2 = __shfl_down_sync(0xffffffffu, v, o);
+    int i2 = __shfl_down_sync(0xffffffffu, idx, o);
+    argmax_pair(v, idx, v2, i2);
+  }
+  if (lane == 0) {
+    sv[wid] = v;
+    si[wid] = idx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T bv = sv[0];
+    int bi = si[0];
+    for (int w = 1; w < nw; ++w) argmax_pair(bv, bi, sv[w], si[w]);
+    sv[0] = bv;
+    si[0] = bi;
+  }
+  __syncthreads();
+  v = sv[0];
+  idx = si[0];
+  __syncthreads();
+}
+
+template <typename T>
+__device__ inline T block_sum(T v, T* sv) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) sv[wid] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T s = 0;
+    for (int w = 0; w < nw; ++w) s += sv[w];
+    sv[0] = s;
+  }
+  __syncthreads();
+  v = sv[0];
+  __syncthreads();
+  return v;
+}
+
+template <typename T>
+__device__ inline T warp_sum(T v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ------------------------------------------------------------------ getrf panel
+// Factor columns k0..k0+jb-1 of every matrix (rows k0..n-1) with partial
+// pivoting, swap whole rows, then U12 = L11^-1 A12.  flags[0] |= 1 on an exact
+// zero pivot, flags[0] |= 2 on a non-finite pivot.
+template <typename T>
+__global__ void __launch_bounds__(256) k_getrf_panel(const MatRef<T>* mats, int nmat, int k0, int* flags) {
+  __shared__ T sv[32];
+  __shared__ int si[32];
+  __shared__ T L11[LU_NB][LU_NB + 1];
+  const int b = blockIdx.x;
+  if (b >= nmat) return;
+  const MatRef<T> M = mats[b];
+  const int n = M.n;
+  if (k0 >= n) return;
+  T* A = M.A;
+  const size_t ld = n;
+  const int jb = min(LU_NB, n - k0);
+  for (int j = k0; j < k0 + jb; ++j) {
+    T best = -1;
+    int bi = n;
+    for (int i = j + threadIdx.x; i < n; i += blockDim.x) {
+      T a = fabs(A[i + j * ld]);
+      if (a != a) a = (T)INFINITY;        // NaN ranks first so it is caught
+      argmax_pair(best, bi, a, i);
+    }
+    block_argmax(best, bi, sv, si);
+    const int p = bi;
+    if (threadIdx.x == 0) M.ipiv[j] = p;
+    if (p != j)
+      for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        T t = A[j + c * ld];
+        A[j + c * ld] = A[p + c * ld];
+        A[p + c * ld] = t;
+      }
+    __syncthreads();
+    const T piv = A[j + j * ld];
+    if (!(piv == piv) || isinf(piv)) {
+      if (threadIdx.x == 0) atomicOr(flags, 2);
+    } else if (piv == (T)0) {
+      if (threadIdx.x == 0) atomicOr(flags, 1);
+    } else {
+      for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+        const T l = A[i + j * ld] / piv;
+        A[i + j * ld] = l;
+        for (int c = j + 1; c < k0 + jb; ++c) A[i + c * ld] -= l * A[j + c * ld];
+      }
+    }
+    __syncthreads();
+  }
+  // U12 = L11^-1 A12
+  for (int t = threadIdx.x; t < jb * jb; t += blockDim.x) {
+    const int r = t % jb, c = t / jb;
+    L11[r][c] = A[(k0 + r) + (size_t)(k0 + c) * ld];
+  }
+  __syncthreads();
+  for (int c = k0 + jb + threadIdx.x; c < n; c += blockDim.x) {
+    T x[LU_NB];
+    T* col = A + (size_t)c * ld + k0;
+#pragma unroll
+    for (int r = 0; r < LU_NB; ++r) x[r] = (r < jb) ? col[r] : (T)0;
+#pragma unroll
+    for (int r = 1; r < LU_NB; ++r) {
+      T s = x[r];
+#pragma unroll
+      for (int q = 0; q < r; ++q) s -= L11[r][q] * x[q];
+      x[r] = s;
+    }
+#pragma unroll
+    for (int r = 0; r < LU_NB; ++r)
+      if (r < jb) col[r] = x[r];
+  }
+}
+
+// permutation from LAPACK-style interchanges: (P^T b)[k] = b[perm[k]]
+template <typename T>
+__global__ void k_ipiv_to_perm(const MatRef<T>* mats, int nmat) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nmat) return;
+  const MatRef<T> M = mats[b];
+  for (int k = 0; k < M.n; ++k) M.perm[k] = k;
+  for (int k = 0; k < M.n; ++k) {
+    int p = M.ipiv[k];
+    int t = M.perm[k];
+    M.perm[k] = M.perm[p];
+    M.perm[p] = t;
+  }
+}
+
+// ------------------------------------------------------------------ grouped GEMM
+template <typename T>
+struct GemmCfg;
+template <>
+struct GemmCfg<double> {
+  static constexpr int BK = 8;
+};
+template <>
+struct GemmCfg<float> {
+  static constexpr int BK = 16;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm(const GemmTask<T>* tasks, const GemmTerm<T>* terms,
+                                              const TileItem* tiles) {
+  constexpr int BM = 64, BN = 64, BK = GemmCfg<T>::BK;
+  __shared__ T As[BK][BM + 4];
+  __shared__ T Bs[BK][BN + 4];
+  const TileItem it = tiles[blockIdx.x];
+  const GemmTask<T> tk = tasks[it.task];
+  const int i0 = it.tm * BM, j0 = it.tn * BN;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = 0;
+  for (int t = tk.t0; t < tk.t1; ++t) {
+    const GemmTerm<T> tm = terms[t];
+    for (int l0 = 0; l0 < tm.k; l0 += BK) {
+      for (int idx = threadIdx.x; idx < BM * BK; idx += 256) {
+        int i, l;
+        if (!tm.ta) { i = idx % BM; l = idx / BM; }
+        else { l = idx % BK; i = idx / BK; }
+        const int gi = i0 + i, gl = l0 + l;
+        T v = 0;
+        if (gi < tk.m && gl < tm.k)
+          v = tm.ta ? tm.A[gl + (size_t)gi * tm.lda] : tm.A[gi + (size_t)gl * tm.lda];
+        As[l][i] = v;
+      }
+      for (int idx = threadIdx.x; idx < BN * BK; idx += 256) {
+        int j, l;
+        if (!tm.tb) { l = idx % BK; j = idx / BK; }
+        else { j = idx % BN; l = idx / BN; }
+        const int gj = j0 + j, gl = l0 + l;
+        T v = 0;
+        if (gj < tk.n && gl < tm.k)
+          v = tm.tb ? tm.B[gj + (size_t)gl * tm.ldb] : tm.B[gl + (size_t)gj * tm.ldb];
+        Bs[l][j] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int l = 0; l < BK; ++l) {
+        T a[4], bb[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) a[r] = As[l][ty * 4 + r];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) bb[c] = Bs[l][tx * 4 + c];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[r][c] += a[r] * bb[c];
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int gj = j0 + tx * 4 + c;
+    if (gj >= tk.n) continue;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int gi = i0 + ty * 4 + r;
+      if (gi >= tk.m) continue;
+      T* cp = tk.C + gi + (size_t)gj * tk.ldc;
+      T v = tk.alpha * acc[r][c];
+      if (tk.beta != (T)0) v += tk.beta * *cp;
+      *cp = v;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ triangular inverses
+// Column tile [j0, j0+32) of L^-1 (unit lower); column k of L^-1 is stored at
+// column perm[k] of F, rows scaled by rs[i] when rs != null:
+//   F = diag(rs) L^-1 P^T.
+template <typename T>
+struct InvTask {
+  const T* LU;       // n x n factors
+  T* out;            // n x n output
+  const int* perm;   // lower: column placement
+  const T* dscale;   // optional: lower -> row scale 1/d_i ; upper -> column scale d_j
+  int n;
+};
+
+struct InvTile {
+  int task, j0;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_inv_lower(const InvTask<T>* tasks, const InvTile* tiles) {
+  __shared__ T Ls[32][33];
+  __shared__ T Xs[32][33];
+  __shared__ T Acc[32][33];
+  const InvTile tl = tiles[blockIdx.x];
+  const InvTask<T> tk = tasks[tl.task];
+  const int n = tk.n, j0 = tl.j0, jb = min(32, n - j0);
+  const size_t ld = n;
+  // output column for local column c
+  __shared__ int ocol[32];
+  if (threadIdx.x < 32) ocol[threadIdx.x] = (threadIdx.x < jb) ? tk.perm[j0 + threadIdx.x] : 0;
+  __syncthreads();
+  // zero rows above j0
+  for (int idx = threadIdx.x; idx < j0 * jb; idx += blockDim.x) {
+    const int r = idx % j0, c = idx / j0;
+    tk.out[r + (size_t)ocol[c] * ld] = 0;
+  }
+  for (int r0 = j0; r0 < n; r0 += 32) {
+    const int rb = min(32, n - r0);
+    // Acc = sum_{q0 in [j0, r0)} L[r0:, q0:] X[q0:, :]
+    for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) Acc[idx % 32][idx / 32] = 0;
+    __syncthreads();
+    for (int q0 = j0; q0 < r0; q0 += 32) {
+      for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
+        const int r = idx % 32, c = idx / 32;
+        Ls[r][c] = (r < rb) ? tk.LU[(r0 + r) + (size_t)(q0 + c) * ld] : (T)0;
+        Xs[r][c] = (c < jb) ? tk.out[(q0 + r) + (size_t)ocol[c] * ld] : (T)0;
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
+        const int r = idx % 32, c = idx / 32;
+        T s = 0;
+#pragma unroll 8
+        for (int q = 0; q < 32; ++q) s += Ls[r][q] * Xs[q][c];
+        Acc[r][c] += s;
+      }
+      __syncthreads();
+    }
+    // diagonal block: X[r0] = Ldiag^-1 (I_part - Acc)
+    for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
+      const int r = idx % 32, c = idx / 32;
+      Ls[r][c] = (r < rb && c < rb) ? tk.LU[(r0 + r) + (size_t)(r0 + c) * ld] : (T)0;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const int c = threadIdx.x;
+      if (c < jb) {
+        T x[32];
+#pragma unroll
+        for (int r = 0; r < 32; ++r) x[r] = ((r0 + r == j0 + c) ? (T)1 : (T)0) - Acc[r][c];
+#pragma unroll
+        for (int r = 1; r < 32; ++r) {
+          T s = x[r];
+#pragma unroll
+          for (int q = 0; q < r; ++q) s -= Ls[r][q] * x[q];
+          x[r] = s;
+        }
+#pragma unroll
+        for (int r = 0; r < 32; ++r)
+          if (r < rb) tk.out[(r0 + r) + (size_t)ocol[c] * ld] = x[r];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Column tile [j0, j0+32) of U^-1 (non-unit upper), column j scaled by dscale[j].
+template <typename T>
+__global__ void __launch_bounds__(256) k_inv_upper(const InvTask<T>* tasks, const InvTile* tiles) {
+  __shared__ T Us[32][33];
+  __shared__ T Xs[32][33];
+  __shared__ T Acc[32][33];
+  const InvTile tl = tiles[blockIdx.x];
+  const InvTask<T> tk = tasks[tl.task];
+  const int n = tk.n, j0 = tl.j0, jb = min(32, n - j0);
+  const size_t ld = n;
+  T* X = tk.out;
+  // zero rows below the tile's diagonal block
+  for (int idx = threadIdx.x; idx < (n - (j0 + 32 < n ? j0 + 32 : n)) * jb; idx += blockDim.x) {
+    const int nz = n - min(n, j0 + 32);
+    const int r = min(n, j0 + 32) + idx % nz, c = idx / nz;
+    X[r + (size_t)(j0 + c) * ld] = 0;
+  }
+  // row blocks from the diagonal block (starting at j0) upward, aligned to j0
+  for (int r0 = j0; r0 >= 0; r0 -= 32) {
+    const int rb = min(32, n - r0);
+    for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) Acc[idx % 32][idx / 32] = 0;
+    __syncthreads();
+    for (int q0 = r0 + 32; q0 < j0 + jb; q0 += 32) {
+      const int qb = min(32, n - q0);
+      for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
+        const int r = idx % 32, c = idx / 32;
+        Us[r][c] = (r < rb && c < qb) ? tk.LU[(r0 + r) + (size_t)(q0 + c) * ld] : (T)0;
+        Xs[r][c] = (r < qb && c < jb) ? X[(q0 + r) + (size_t)(j0 + c) * ld] : (T)0;
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
+        const int r = idx % 32, c = idx / 32;
+        T s = 0;
+#pragma unroll 8
+        for (int q = 0; q < 32; ++q) s += Us[r][q] * Xs[q][c];
+        Acc[r][c] += s;
+      }
+      __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
+      const int r = idx % 32, c = idx / 32;
+      Us[r][c] = (r < rb && c < rb) ? tk.LU[(r0 + r) + (size_t)(r0 + c) * ld] : (T)1;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const int c = threadIdx.x;
+      if (c < jb) {
+        const T dsc = tk.dscale ? tk.dscale[j0 + c] : (T)1;
+        T x[32];
+#pragma unroll
+        for (int r = 0; r < 32; ++r) x[r] = ((r0 + r == j0 + c) ? dsc : (T)0) - Acc[r][c];
+#pragma unroll
+        for (int r = 31; r >= 0; --r) {
+          T s = x[r];
+#pragma unroll
+          for (int q = r + 1; q < 32; ++q) s -= Us[r][q] * x[q];
+          x[r] = (r < rb) ? s / Us[r][r] : (T)0;
+        }
+#pragma unroll
+        for (int r = 0; r < 32; ++r)
+          if (r < rb) X[(r0 + r) + (size_t)(j0 + c) * ld] = x[r];
+      }
+    }
+    __syncthreads();
+    if (r0 == 0) break;
+  }
+}
+
+// rows of out scaled by 1 / dscale[i]  (diag(|d|^-1/2) applied to L^-1 P^T)
+template <typename T>
+__global__ void k_scale_rows(const InvTask<T>* tasks, const InvTile* tiles) {
+  const InvTile tl = tiles[blockIdx.x];
+  const InvTask<T> tk = tasks[tl.task];
+  if (!tk.dscale) return;
+  const int n = tk.n, jb = min(32, n - tl.j0);
+  for (int idx = threadIdx.x; idx < n * jb; idx += blockDim.x) {
+    const int r = idx % n, c = tl.j0 + idx / n;
+    tk.out[r + (size_t)c * n] /= tk.dscale[r];
+  }
+}
+
+// d[i] = sqrt(|U_ii|)
+template <typename T>
+__global__ void k_diag_sqrt(const MatRef<T>* mats, T* const* dout, int nmat) {
+  const int b = blockIdx.x;
+  if (b >= nmat) return;
+  const MatRef<T> M = mats[b];
+  for (int i = threadIdx.x; i < M.n; i += blockDim.x) dout[b][i] = sqrt(fabs(M.A[i + (size_t)i * M.n]));
+}
+
+// ------------------------------------------------------------------ copies
+template <typename T>
+__global__ void k_copy_tiles(const CopyTask<T>* tasks, const CopyTile* tiles) {
+  __shared__ T tile[32][33];
+  const CopyTile ct = tiles[blockIdx.x];
+  const CopyTask<T> tk = tasks[ct.task];
+  const int r0 = ct.tr * 32, c0 = ct.tc * 32;
+  if (!tk.trans) {
+    for (int idx = threadIdx.x; idx < 1024; idx += blockDim.x) {
+      const int r = r0 + (idx & 31), c = c0 + (idx >> 5);
+      if (r < tk.rows && c < tk.cols) tk.dst[r + (size_t)c * tk.ldd] = tk.src[r + (size_t)c * tk.lds];
+    }
+  } else {
+    // dst (rows x cols) = src^T, src is cols x rows
+    for (int idx = threadIdx.x; idx < 1024; idx += blockDim.x) {
+      const int sr = c0 + (idx & 31), sc = r0 + (idx >> 5);
+      if (sr < tk.cols && sc < tk.rows) tile[idx >> 5][idx & 31] = tk.src[sr + (size_t)sc * tk.lds];
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 1024; idx += blockDim.x) {
+      const int r = r0 + (idx & 31), c = c0 + (idx >> 5);
+      if (r < tk.rows && c < tk.cols) tk.dst[r + (size_t)c * tk.ldd] = tile[idx & 31][idx >> 5];
+    }
+  }
+}
+
+// dst = I_r at (dst, ldd)
+template <typename T>
+struct EyeTask {
+  T* dst;
+  int ldd, r;
+};
+
+template <typename T>
+__global__ void k_eye(const EyeTask<T>* tasks, int ntask) {
+  for (int t = blockIdx.x; t < ntask; t += gridDim.x) {
+    const EyeTask<T> tk = tasks[t];
+    for (int i = threadIdx.x; i < tk.r; i += blockDim.x) tk.dst[i + (size_t)i * tk.ldd] = (T)1;
+  }
+}
+
+// ------------------------------------------------------------------ RRQR
+// Column-pivoted Householder QR of W (n x c) stopped at the first k with
+// |R_kk| <= eps |R_00| (or R_00 = 0); writes the rank, tau and the reflectors.
+// Column norms are recomputed exactly in the update pass.  Dynamic shared
+// memory holds the current reflector (n values).
+template <typename T>
+__global__ void __launch_bounds__(256) k_qrcp(const QrTask<T>* tasks, T eps) {
+  extern __shared__ unsigned char qr_smem[];
+  T* v = reinterpret_cast<T*>(qr_smem);
+  __shared__ T sv[32];
+  __shared__ int si[32];
+  __shared__ T s_tau;
+  const QrTask<T> tk = tasks[blockIdx.x];
+  const int n = tk.n, c = tk.c;
+  const size_t ld = n;
+  T* W = tk.W;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = wid; j < c; j += nw) {
+    T s = 0;
+    for (int i = lane; i < n; i += 32) {
+      T a = W[i + j * ld];
+      s += a * a;
+    }
+    s = warp_sum(s);
+    if (lane == 0) tk.norm2[j] = s;
+  }
+  __syncthreads();
+  const int kmax = min(n, c);
+  T nrm0 = 0;
+  int rank = kmax;
+  for (int k = 0; k < kmax; ++k) {
+    T best = -1;
+    int bi = c;
+    for (int j = k + threadIdx.x; j < c; j += blockDim.x) argmax_pair(best, bi, tk.norm2[j], j);
+    block_argmax(best, bi, sv, si);
+    const T nrm = sqrt(fmax(best, (T)0));
+    if (k == 0) nrm0 = nrm;
+    if (nrm0 == (T)0 || (k > 0 && nrm <= eps * nrm0)) {
+      rank = k;
+      break;
+    }
+    const int p = bi;
+    if (p != k) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        T t = W[i + k * ld];
+        W[i + k * ld] = W[i + p * ld];
+        W[i + p * ld] = t;
+      }
+      if (threadIdx.x == 0) {
+        T t = tk.norm2[k];
+        tk.norm2[k] = tk.norm2[p];
+        tk.norm2[p] = t;
+      }
+    }
+    __syncthreads();
+    // Householder reflector of W[k:, k]
+    T part = 0;
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) {
+      T a = W[i + k * ld];
+      part += a * a;
+    }
+    const T sigma = block_sum(part, sv);
+    const T alpha = W[k + k * ld];
+    T tau = 0, beta = alpha, scale = 0;
+    if (sigma > (T)0) {
+      beta = -copysign(sqrt(alpha * alpha + sigma), alpha);
+      tau = (beta - alpha) / beta;
+      scale = (T)1 / (alpha - beta);
+    }
+    for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+      T vi;
+      if (i == k) vi = (T)1;
+      else vi = W[i + k * ld] * scale;
+      v[i - k] = vi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      W[k + k * ld] = beta;
+      tk.tau[k] = tau;
+      s_tau = tau;
+    }
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) W[i + k * ld] = v[i - k];
+    __syncthreads();
+    // apply H = I - tau v v^T to the trailing columns and refresh their norms
+    for (int j = k + 1 + wid; j < c; j += nw) {
+      T* col = W + j * ld;
+      T dot = 0;
+      for (int i = k + lane; i < n; i += 32) dot += v[i - k] * col[i];
+      dot = warp_sum(dot) * s_tau;
+      T s = 0;
+      for (int i = k + lane; i < n; i += 32) {
+        T a = col[i] - dot * v[i - k];
+        col[i] = a;
+        if (i > k) s += a * a;
+      }
+      s = warp_sum(s);
+      if (lane == 0) tk.norm2[j] = s;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *tk.rank = rank;
+}
+
+// explicit Q_c = H_0 ... H_{r-1} [I_r; 0]  (n x r, ld = n)
+template <typename T>
+__global__ void __launch_bounds__(256) k_form_q(const QrTask<T>* tasks) {
+  const QrTask<T> tk = tasks[blockIdx.x];
+  const int n = tk.n, r = *tk.rank;
+  const size_t ld = n;
+  T* Q = tk.Q;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int idx = threadIdx.x; idx < n * r; idx += blockDim.x) {
+    const int i = idx % n, j = idx / n;
+    Q[i + (size_t)j * ld] = (i == j) ? (T)1 : (T)0;
+  }
+  __syncthreads();
+  for (int k = r - 1; k >= 0; --k) {
+    const T tau = tk.tau[k];
+    const T* vk = tk.W + (size_t)k * ld;   // v_k[k] = 1 implicit, below-diagonal stored
+    for (int j = k + wid; j < r; j += nw) {
+      T* col = Q + (size_t)j * ld;
+      T dot = 0;
+      for (int i = k + lane; i < n; i += 32) dot += ((i == k) ? (T)1 : vk[i]) * col[i];
+      dot = warp_sum(dot) * tau;
+      for (int i = k + lane; i < n; i += 32) col[i] -= dot * ((i == k) ? (T)1 : vk[i]);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace spand

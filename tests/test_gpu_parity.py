@@ -1,0 +1,237 @@
+"""GPU parity tests: every step of the CUDA path against the CPU oracle on the
+same seeded inputs, through the C ABI.
+
+Tolerances (derived in the design notes): assembly is FP64 with a different
+summation order -> 1e-11 relative; eps=0 spaND is an exact direct solve ->
+backward error 1e-12; solutions -> true relative residual <= 1e-8 and error
+<= 1e-6 against a dense / eps=0 solve; s-step iterates vs GMRES -> 1e-10.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import dg, spand  # noqa: E402
+from oracle.gmres import sstep_gmres as o_sstep  # noqa: E402
+from synth import get_config, modal_state, naca_ogrid  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def sg():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2101_01763_gb300 as m
+    return m
+
+
+def _case(nt, nr, p, seed, mach=0.5, alpha=2.0, amp=0.05, cfl=10.0, bc="wall"):
+    X = naca_ogrid(nt, nr, seed)
+    u = modal_state(X, p, mach, alpha, amp, seed)
+    return X, u, dict(mach=mach, alpha_deg=alpha, cfl=cfl)
+
+
+def _gpu_assemble(sg, X, u, p, fl, bc="wall"):
+    dev = torch.device("cuda")
+    return sg.assemble(torch.as_tensor(X, device=dev), p, torch.as_tensor(u, device=dev), fl["mach"],
+                       fl["alpha_deg"], fl["cfl"], bc=bc)
+
+
+@pytest.mark.parametrize("nt,nr,p,bc", [(16, 8, 1, "wall"), (12, 5, 2, "wall"), (8, 4, 3, "farfield"),
+                                         (20, 6, 3, "wall")])
+def test_assembly_matches_oracle(sg, nt, nr, p, bc):
+    X, u, fl = _case(nt, nr, p, 100 + nt + p)
+    rhs, A, dtau = _gpu_assemble(sg, X, u, p, fl, bc)
+    rhs_o, (rp, col, val), dtau_o = dg.assemble(X, p, u, fl["mach"], fl["alpha_deg"], fl["cfl"], bc_mode=bc)
+    assert abs(dtau - dtau_o) <= 1e-13 * dtau_o
+    assert np.array_equal(A.row_ptr.cpu().numpy(), rp)
+    assert np.array_equal(A.col.cpu().numpy(), col)
+    vg = A.blocks_rowmajor()
+    scale = np.abs(val).max()
+    assert np.abs(vg - val).max() <= 1e-12 * scale
+    r = rhs.cpu().numpy()
+    assert np.abs(r - rhs_o).max() <= 1e-12 * max(1.0, np.abs(rhs_o).max())
+
+
+def test_assembly_freestream_zero(sg):
+    from synth import uniform_modal_state
+    X = naca_ogrid(16, 8, 3)
+    u = uniform_modal_state(128, 2, 0.5, 2.0)
+    rhs, A, _ = _gpu_assemble(sg, X, u, 2, dict(mach=0.5, alpha_deg=2.0, cfl=10.0), bc="farfield")
+    assert rhs.abs().max().item() <= 1e-12
+
+
+@pytest.mark.parametrize("transpose", [False, True])
+def test_spmv_matches_scipy(sg, transpose):
+    X, u, fl = _case(16, 8, 2, 7)
+    _, bsr, _ = dg.assemble(X, 2, u, fl["mach"], fl["alpha_deg"], fl["cfl"])
+    A = sg.BSR.from_host(*bsr)
+    S = dg.bsr_to_scipy(*bsr).tocsr()
+    x = np.random.default_rng(0).standard_normal(S.shape[0])
+    y = sg.spmv(A, torch.as_tensor(x, device="cuda"), transpose=transpose).cpu().numpy()
+    ref = (S.T @ x) if transpose else (S @ x)
+    assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.fixture(scope="module")
+def c1(sg):
+    # the oracle's matrix through the C ABI: solver parity does not depend on assembly parity
+    c = get_config("C1")
+    X, u, fl = _case(c.n_theta, c.n_r, c.p, c.seed, c.mach, c.alpha_deg, c.amp, c.cfl)
+    rhs_o, bsr, _ = dg.assemble(X, c.p, u, c.mach, c.alpha_deg, c.cfl)
+    A = sg.BSR.from_host(*bsr)
+    rhs = torch.as_tensor(rhs_o, device="cuda")
+    S = dg.bsr_to_scipy(*bsr).tocsr()
+    return c, rhs, A, rhs_o, bsr, S
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_spand_eps0_direct_solve(sg, c1, prec):
+    c, rhs, A, rhs_o, bsr, S = c1
+    plan = sg.Plan(c.n_theta, c.n_r, c.B, c.nd_depth)
+    F = sg.Factor(plan, A, 0.0, prec)
+    z = F.apply(rhs).cpu().numpy()
+    Ad = S.toarray()
+    berr = np.linalg.norm(Ad @ z - rhs_o) / (np.linalg.norm(Ad, 2) * np.linalg.norm(z) + np.linalg.norm(rhs_o))
+    assert berr <= (1e-12 if prec == "fp64" else 1e-5)
+    st = F.stats()
+    assert st["sum_r"] == st["sum_n"]          # eps = 0 keeps every DOF
+
+
+def test_spand_apply_matches_oracle_operator_eps0_tiny(sg):
+    X, u, fl = _case(8, 4, 1, 5)
+    _, bsr, _ = dg.assemble(X, 1, u, fl["mach"], fl["alpha_deg"], fl["cfl"])
+    A = sg.BSR.from_host(*bsr)
+    Ad = dg.bsr_to_dense(*bsr)
+    F = sg.Factor(sg.Plan(8, 4, 16, 2), A, 0.0, "fp64")
+    E = torch.eye(Ad.shape[0], dtype=torch.float64, device="cuda")
+    Minv = torch.stack([F.apply(E[i].contiguous()) for i in range(Ad.shape[0])], 1).cpu().numpy()
+    assert np.allclose(Minv @ Ad, np.eye(Ad.shape[0]), atol=1e-10)
+    MinvT = torch.stack([F.apply(E[i].contiguous(), transpose=True) for i in range(Ad.shape[0])], 1).cpu().numpy()
+    assert np.allclose(MinvT, Minv.T, atol=1e-11)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_spand_eps_transpose_identity(sg, c1, prec):
+    c, rhs, A, rhs_o, bsr, S = c1
+    F = sg.Factor(sg.Plan(c.n_theta, c.n_r, c.B, c.nd_depth), A, c.eps, prec)
+    rng = np.random.default_rng(1)
+    v = torch.as_tensor(rng.standard_normal(c.N), device="cuda")
+    w = torch.as_tensor(rng.standard_normal(c.N), device="cuda")
+    lhs = torch.dot(F.apply(v), w).item()
+    rhs_ = torch.dot(v, F.apply(w, transpose=True)).item()
+    assert abs(lhs - rhs_) <= (1e-10 if prec == "fp64" else 1e-4) * abs(lhs)
+
+
+def test_spand_eps_preconditioner_quality_matches_oracle(sg, c1):
+    """eps > 0: ranks may differ from the oracle on ties, so compare what the
+    factorization is for: the residual of one preconditioner application."""
+    c, rhs, A, rhs_o, bsr, S = c1
+    F = sg.Factor(sg.Plan(c.n_theta, c.n_r, c.B, c.nd_depth), A, c.eps, "fp64")
+    z = F.apply(rhs).cpu().numpy()
+    Fo = spand.factor(bsr, c.n_theta, c.n_r, c.nd_depth, c.eps)
+    zo = spand.apply(Fo, rhs_o)
+    rg = np.linalg.norm(S @ z - rhs_o) / np.linalg.norm(rhs_o)
+    ro = np.linalg.norm(S @ zo - rhs_o) / np.linalg.norm(rhs_o)
+    assert rg <= 10 * ro + 1e-12
+    st = F.stats()
+    oranks = [sum(b for _, b in lv) for lv in Fo.ranks]
+    for l, r in enumerate(oranks):
+        assert abs(st["sum_r"][l] - r) <= max(2, 0.02 * r)
+
+
+@pytest.mark.parametrize("basis", ["newton", "monomial"])
+def test_sstep_gmres_iterates_match_oracle(sg, c1, basis):
+    """Unpreconditioned s-step GMRES on the C1 Jacobian, stopped after k columns."""
+    c, rhs, A, rhs_o, bsr, S = c1
+    for k in (4, 8, 16):
+        xg, st = sg.sstep_gmres(A, None, rhs, s=4, restart=k, tol=0.0, max_iters=k, basis=basis)
+        xo, so = o_sstep(lambda v: S @ v, lambda v: v, rhs_o, s=4, restart=k, tol=0.0, max_iters=k, basis=basis)
+        assert st["iters"] == so.iters == k
+        xg = xg.cpu().numpy()
+        assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_c1_full_solve(sg, c1, prec):
+    c, rhs, A, rhs_o, bsr, S = c1
+    F = sg.Factor(sg.Plan(c.n_theta, c.n_r, c.B, c.nd_depth), A, c.eps, prec)
+    x, st = sg.sstep_gmres(A, F, rhs, s=c.s, restart=c.restart, tol=c.tol, max_iters=c.max_iters)
+    x = x.cpu().numpy()
+    assert st["converged"]
+    relres = np.linalg.norm(S @ x - rhs_o) / np.linalg.norm(rhs_o)
+    xd = np.linalg.solve(S.toarray(), rhs_o)
+    assert relres <= 1e-8
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 1e-6
+
+
+def test_stress_eps_many_blocks(sg, c1):
+    """Crude preconditioner (eps=0.5) forces several s-blocks and restarts."""
+    c, rhs, A, rhs_o, bsr, S = c1
+    F = sg.Factor(sg.Plan(c.n_theta, c.n_r, c.B, c.nd_depth), A, 0.5, "fp64")
+    x, st = sg.sstep_gmres(A, F, rhs, s=4, restart=8, tol=1e-10, max_iters=400)
+    x = x.cpu().numpy()
+    assert st["converged"] and st["reductions"] >= 2
+    xd = np.linalg.solve(S.toarray(), rhs_o)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 1e-7
+
+
+def test_transposed_solve(sg, c1):
+    c, rhs, A, rhs_o, bsr, S = c1
+    F = sg.Factor(sg.Plan(c.n_theta, c.n_r, c.B, c.nd_depth), A, c.eps, "fp64")
+    w = np.random.default_rng(3).standard_normal(c.N)
+    lam, st = sg.sstep_gmres(A, F, torch.as_tensor(w, device="cuda"), s=c.s, restart=c.restart, tol=1e-12,
+                             transpose=True)
+    lam = lam.cpu().numpy()
+    ref = np.linalg.solve(S.toarray().T, w)
+    assert st["converged"] and np.linalg.norm(lam - ref) / np.linalg.norm(ref) <= 1e-9
+
+
+def test_error_paths_do_not_hang(sg, c1):
+    c, rhs, A, rhs_o, bsr, S = c1
+    # unreachable tolerance -> NOT_CONVERGED after max_iters, x finite
+    x, st = sg.sstep_gmres(A, None, rhs, s=4, restart=8, tol=1e-30, max_iters=16)
+    assert not st["converged"] and torch.isfinite(x).all()
+    # a NaN in A -> non-finite status from the factorization
+    A2 = sg.BSR(A.K, A.B, A.row_ptr, A.col, A.val.clone())
+    A2.val[5] = float("nan")
+    with pytest.raises(sg.SpandError) as ei:
+        sg.Factor(sg.Plan(c.n_theta, c.n_r, c.B, c.nd_depth), A2, c.eps, "fp64")
+    assert ei.value.status == -5
+    # a zero diagonal block row -> zero pivot
+    A3 = sg.BSR(A.K, A.B, A.row_ptr, A.col, A.val.clone())
+    rp = A.row_ptr.cpu().numpy()
+    cl = A.col.cpu().numpy()
+    e = 3
+    v = A3.val.view(-1, c.B, c.B)
+    for k in range(rp[e], rp[e + 1]):
+        v[k, :, 0] = 0.0        # column-major block: [k, col, row] -> zero row 0 of element 3
+    del cl
+    with pytest.raises(sg.SpandError) as ei:
+        sg.Factor(sg.Plan(c.n_theta, c.n_r, c.B, c.nd_depth), A3, 0.0, "fp64")
+    assert ei.value.status == -3
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_c2_full_size_properties(sg, prec):
+    """Bench workload (p=2, 64x32, N=73,728): assembly vs the oracle, true FP64
+    residual of the solution <= 1e-8 and agreement with an independent solve."""
+    c = get_config("C2")
+    X, u, fl = _case(c.n_theta, c.n_r, c.p, c.seed, c.mach, c.alpha_deg, c.amp, c.cfl)
+    rhs, A, dtau = _gpu_assemble(sg, X, u, c.p, fl)
+    rhs_o, bsr, dtau_o = dg.assemble(X, c.p, u, c.mach, c.alpha_deg, c.cfl)
+    assert abs(dtau - dtau_o) <= 1e-13 * dtau_o
+    assert np.abs(A.blocks_rowmajor() - bsr[2]).max() <= 1e-12 * np.abs(bsr[2]).max()
+    S = dg.bsr_to_scipy(*bsr).tocsr()
+    F = sg.Factor(sg.Plan(c.n_theta, c.n_r, c.B, c.nd_depth), A, c.eps, prec)
+    x, st = sg.sstep_gmres(A, F, rhs, s=c.s, restart=c.restart, tol=c.tol, max_iters=c.max_iters)
+    x = x.cpu().numpy()
+    relres = np.linalg.norm(S @ x - rhs_o) / np.linalg.norm(rhs_o)
+    assert st["converged"] and relres <= 1e-8
+    # independent reference: sparse direct solve (SuperLU) of the same matrix
+    import scipy.sparse.linalg as spla
+    xr = spla.spsolve(S.tocsc(), rhs_o)
+    assert np.linalg.norm(x - xr) / np.linalg.norm(xr) <= 1e-6
+
