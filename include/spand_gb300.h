@@ -131,9 +131,8 @@ int spand_plan_export(spand_plan_t plan, int* owner, int* node_level, int* table
  * rank r = #{k : |R_kk| > eps |R_00|}, compress every block to
  * Q_ic^T A_ij Q_jc and merge.  eps = 0 gives an exact direct factorization.
  * precision: SPAND_FP64 (all factor arithmetic in FP64) or SPAND_MIXED
- * (factors computed and stored in FP32; the FP32 GEMMs of the Schur,
- * scaling and compression updates use TF32 tensor cores with FP32
- * accumulation).  A is read only; the factor owns its device memory.
+ * (factors computed and stored in FP32 with FP32 accumulation; the outer
+ * GMRES stays FP64 and acts as iterative refinement).  A is read only; the factor owns its device memory.
  * Errors: SPAND_ERR_ARG, SPAND_ERR_NOMEM, SPAND_ERR_ZERO_PIVOT,
  * SPAND_ERR_NONFINITE, SPAND_ERR_CUDA. */
 typedef struct spand_factor_s* spand_factor_t;
