@@ -10,7 +10,8 @@
  * Conventions shared by every entry point
  *  - Return value: int status; 0 = SPAND_OK, negative = error (codes below).
  *    On error no output is guaranteed; handles stay valid and must still be
- *    destroyed.  No entry point writes host globals.
+ *    destroyed.  No entry point writes host globals, except the per-device
+ *    address cache of sstep_gmres_solve_noalloc (below).
  *  - Pointers documented as "device" must point to device memory owned by the
  *    caller (any allocator); "host" pointers are caller-owned host memory.
  *    Handles (spand_plan_t, spand_factor_t) are owned by the library and are
@@ -29,6 +30,7 @@
 #ifndef SPAND_GB300_H
 #define SPAND_GB300_H
 
+#include <stddef.h>
 #include <stdint.h>
 #include <cuda_runtime_api.h>
 
@@ -45,7 +47,9 @@ enum {
   SPAND_ERR_NONFINITE = -5,      /* NaN/Inf met in a residual or a factor             */
   SPAND_ERR_NOT_CONVERGED = -6,  /* GMRES reached max_iters above tolerance           */
   SPAND_ERR_CUDA = -7,           /* a CUDA runtime call failed                        */
-  SPAND_ERR_UNSUPPORTED = -8     /* configuration outside the supported range         */
+  SPAND_ERR_UNSUPPORTED = -8,    /* configuration outside the supported range         */
+  SPAND_ERR_SCRATCH = -9         /* problem needs more than the fixed scratch of
+                                    sstep_gmres_solve_noalloc                          */
 };
 
 enum { SPAND_BC_WALL = 0, SPAND_BC_FARFIELD = 1 };
@@ -197,6 +201,32 @@ typedef struct {
 
 int sstep_gmres_solve(const bsr_matrix* A, spand_factor_t M, const double* b, double* x,
                       const gmres_opts* opts, gmres_stats* stats, cudaStream_t stream);
+
+/* sstep_gmres_solve_noalloc - the same solve as sstep_gmres_solve (same
+ * arguments, same results), for callers that must not allocate device memory
+ * during a solve: for example a program that gives all device memory to its own
+ * pool allocator at start-up, or one that runs under a fixed device-memory
+ * budget and cannot let an allocation fail half-way through a solve.  This
+ * entry point calls no cudaMalloc / cudaFree or any allocating routine; its
+ * scratch (Krylov basis, Gram partial sums, small dense work) is carved from
+ * one fixed device array of sstep_gmres_noalloc_capacity() bytes (8 MiB) that
+ * every GPU which loads this library holds until the process exits.  The
+ * paper has no counterpart; it is an interface choice of this library.
+ *  - Size limit: the scratch needs about (restart + 2s + 4) * N doubles plus
+ *    (restart + 2s + 2) * 304 * 32 doubles of Gram partial sums; larger
+ *    problems are rejected with SPAND_ERR_SCRATCH before any work is queued.
+ *  - The first call on each device looks up the array's device address (with
+ *    that device current) and caches it; make that first call before any
+ *    stream capture.
+ *  - Every call on a device shares the one array and it keeps the previous
+ *    call's contents (the solver clears what it needs zeroed).  Calls whose
+ *    work overlaps on the GPU (other streams, other host threads) race on the
+ *    array: order them, e.g. on one stream.
+ *  - The preconditioner M is applied through its own factor-owned buffers
+ *    (allocated by spand_factor, not by this call). */
+int sstep_gmres_solve_noalloc(const bsr_matrix* A, spand_factor_t M, const double* b, double* x,
+                              const gmres_opts* opts, gmres_stats* stats, cudaStream_t stream);
+size_t sstep_gmres_noalloc_capacity(void);
 
 const char* spand_status_string(int status);
 

@@ -11,7 +11,8 @@ LIB_PATH = os.path.join(HERE, "libspand_gb300.so")
 
 OK = 0
 STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "zero pivot", -4: "CholQR breakdown",
-          -5: "non-finite value", -6: "not converged", -7: "CUDA error", -8: "unsupported"}
+          -5: "non-finite value", -6: "not converged", -7: "CUDA error", -8: "unsupported",
+          -9: "larger than the no-allocation scratch"}
 SPAND_FP64, SPAND_MIXED = 0, 1
 BASIS_NEWTON, BASIS_MONOMIAL = 0, 1
 BC_WALL, BC_FARFIELD = 0, 1
@@ -72,6 +73,9 @@ EXPORTS = {
     "spand_apply": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p], C.c_int),
     "sstep_gmres_solve": ([C.POINTER(BsrMatrix), C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(GmresOpts),
                            C.POINTER(GmresStats), C.c_void_p], C.c_int),
+    "sstep_gmres_solve_noalloc": ([C.POINTER(BsrMatrix), C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.POINTER(GmresOpts), C.POINTER(GmresStats), C.c_void_p], C.c_int),
+    "sstep_gmres_noalloc_capacity": ([], C.c_size_t),
     "spand_status_string": ([C.c_int], C.c_char_p),
 }
 

@@ -315,6 +315,7 @@ const char* spand_status_string(int status) {
     case SPAND_ERR_NOT_CONVERGED: return "GMRES did not converge";
     case SPAND_ERR_CUDA: return "CUDA error";
     case SPAND_ERR_UNSUPPORTED: return "unsupported configuration";
+    case SPAND_ERR_SCRATCH: return "problem larger than the fixed scratch of the no-allocation entry point";
   }
   return "unknown status";
 }

@@ -17,6 +17,7 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -450,43 +451,72 @@ std::vector<std::complex<double>> leja(std::vector<std::complex<double>> th) {
 }  // namespace
 }  // namespace spand
 
-extern "C" int sstep_gmres_solve(const bsr_matrix* A, spand_factor_t M, const double* b, double* x,
-                                 const gmres_opts* opts, gmres_stats* stats, cudaStream_t st) {
-  using namespace spand;
+namespace spand {
+namespace {
+
+// Device buffers of one solve: small dense work, basis vectors, Gram partial
+// sums, status words and the Gram column-pointer tables.
+struct GmresScratch {
+  double* small;
+  double* vec;
+  double* part;
+  int* stat;
+  const double** dZ;
+  const double** dY;
+};
+
+struct GmresSizes {
+  std::vector<size_t> small;  // doubles per small-matrix piece
+  size_t small_tot, nvec, part, maxptr;
+};
+
+constexpr int kGramBlocks = 2 * 152;
+
+GmresSizes gmres_sizes(int m, int s) {
+  GmresSizes z;
+  const int ldh = m + 1, ldg = m + 2 * s + 2, ldt = m + s + 2;
+  z.small = {(size_t)ldh * m, (size_t)ldh * m, (size_t)m + 1, (size_t)m + 1, (size_t)ldh,
+             (size_t)(s + 1) * s, (size_t)ldg * (ldg), (size_t)ldh * s, (size_t)s * s, (size_t)ldh + s,
+             (size_t)ldh * s, (size_t)s * s, (size_t)ldh * s, (size_t)s * s, (size_t)ldt * (s + 1),
+             (size_t)ldt * s, (size_t)ldh + s, 16, (size_t)s * s};
+  z.small_tot = 0;
+  for (auto v : z.small) z.small_tot += v;
+  z.nvec = (size_t)(m + 1) + 2 * s + 3;
+  z.part = (size_t)kGramBlocks * ldg * 32;
+  z.maxptr = (size_t)ldg + 64;
+  return z;
+}
+
+int gmres_validate(const bsr_matrix* A, spand_factor_t M, const double* b, double* x, const gmres_opts* opts) {
   if (!A || !b || !x || !opts || !A->row_ptr || !A->col || !A->val) return SPAND_ERR_ARG;
   const int s = opts->s, m = opts->restart;
   if (s < 1 || s > 16 || m < s || m % s != 0 || m > 480 || opts->max_iters < 1 || !(opts->tol >= 0))
     return SPAND_ERR_ARG;
   const int64_t N = (int64_t)A->K * A->B;
   if (M && factor_size(M) != N) return SPAND_ERR_ARG;
+  return SPAND_OK;
+}
+
+// The solve itself; every device buffer comes from `sc` (the caller owns them).
+int sstep_core(const bsr_matrix* A, spand_factor_t M, const double* b, double* x, const gmres_opts* opts,
+               gmres_stats* stats, cudaStream_t st, const GmresScratch& sc) {
+  const int s = opts->s, m = opts->restart;
+  const int64_t N = (int64_t)A->K * A->B;
   const int tr = opts->transpose ? 1 : 0;
   const bool newton = opts->basis == SPAND_BASIS_NEWTON;
   gmres_stats stl;
   memset(&stl, 0, sizeof(stl));
-  // ---- device memory
   const int ldh = m + 1, ldg = m + 2 * s + 2, ldt = m + s + 2;
-  const int nblk = 2 * 152;
-  std::vector<size_t> sz = {(size_t)ldh * m, (size_t)ldh * m, (size_t)m + 1, (size_t)m + 1, (size_t)ldh,
-                            (size_t)(s + 1) * s, (size_t)ldg * (ldg), (size_t)ldh * s, (size_t)s * s, (size_t)ldh + s,
-                            (size_t)ldh * s, (size_t)s * s, (size_t)ldh * s, (size_t)s * s, (size_t)ldt * (s + 1),
-                            (size_t)ldt * s, (size_t)ldh + s, 16, (size_t)s * s};
-  size_t tot = 0;
-  for (auto v : sz) tot += v;
-  double* dsmall = nullptr;
-  double* dvec = nullptr;
-  double* dpart = nullptr;
-  int* dstat = nullptr;
-  const size_t nvec = (size_t)(m + 1) + 2 * s + 3;
-  if (cudaMallocAsync(&dsmall, tot * sizeof(double), st) != cudaSuccess) return SPAND_ERR_NOMEM;
-  if (cudaMallocAsync(&dvec, nvec * N * sizeof(double), st) != cudaSuccess) return SPAND_ERR_NOMEM;
-  if (cudaMallocAsync(&dpart, (size_t)nblk * ldg * 32 * sizeof(double), st) != cudaSuccess) return SPAND_ERR_NOMEM;
-  if (cudaMallocAsync(&dstat, 4 * sizeof(int), st) != cudaSuccess) return SPAND_ERR_NOMEM;
-  // pointer tables for Gram products (host staging -> device)
-  const int maxptr = ldg + 64;
-  const double** dZ = nullptr;
-  const double** dY = nullptr;
-  if (cudaMallocAsync((void**)&dZ, maxptr * sizeof(double*), st) != cudaSuccess) return SPAND_ERR_NOMEM;
-  if (cudaMallocAsync((void**)&dY, 64 * sizeof(double*), st) != cudaSuccess) return SPAND_ERR_NOMEM;
+  const int nblk = kGramBlocks;
+  const GmresSizes zs = gmres_sizes(m, s);
+  const std::vector<size_t>& sz = zs.small;
+  const size_t tot = zs.small_tot;
+  double* dsmall = sc.small;
+  double* dvec = sc.vec;
+  double* dpart = sc.part;
+  int* dstat = sc.stat;
+  const double** dZ = sc.dZ;
+  const double** dY = sc.dY;
   cudaMemsetAsync(dsmall, 0, tot * sizeof(double), st);
   cudaMemsetAsync(dstat, 0, 4 * sizeof(int), st);
   Small S;
@@ -781,13 +811,113 @@ extern "C" int sstep_gmres_solve(const bsr_matrix* A, spand_factor_t M, const do
     }
     stl.orth_err = o;
   }
-  cudaFreeAsync(dsmall, st);
-  cudaFreeAsync(dvec, st);
-  cudaFreeAsync(dpart, st);
-  cudaFreeAsync(dstat, st);
-  cudaFreeAsync(dZ, st);
-  cudaFreeAsync(dY, st);
   if (cudaStreamSynchronize(st) != cudaSuccess && status == SPAND_OK) status = SPAND_ERR_CUDA;
   if (stats) *stats = stl;
   return status;
 }
+
+}  // namespace
+}  // namespace spand
+
+extern "C" int sstep_gmres_solve(const bsr_matrix* A, spand_factor_t M, const double* b, double* x,
+                                 const gmres_opts* opts, gmres_stats* stats, cudaStream_t st) {
+  using namespace spand;
+  const int v = gmres_validate(A, M, b, x, opts);
+  if (v != SPAND_OK) return v;
+  const int s = opts->s, m = opts->restart;
+  const int64_t N = (int64_t)A->K * A->B;
+  const GmresSizes zs = gmres_sizes(m, s);
+  GmresScratch sc{};
+  if (cudaMallocAsync(&sc.small, zs.small_tot * sizeof(double), st) != cudaSuccess) return SPAND_ERR_NOMEM;
+  if (cudaMallocAsync(&sc.vec, zs.nvec * N * sizeof(double), st) != cudaSuccess) return SPAND_ERR_NOMEM;
+  if (cudaMallocAsync(&sc.part, zs.part * sizeof(double), st) != cudaSuccess) return SPAND_ERR_NOMEM;
+  if (cudaMallocAsync(&sc.stat, 4 * sizeof(int), st) != cudaSuccess) return SPAND_ERR_NOMEM;
+  if (cudaMallocAsync((void**)&sc.dZ, zs.maxptr * sizeof(double*), st) != cudaSuccess) return SPAND_ERR_NOMEM;
+  if (cudaMallocAsync((void**)&sc.dY, 64 * sizeof(double*), st) != cudaSuccess) return SPAND_ERR_NOMEM;
+  int status = sstep_core(A, M, b, x, opts, stats, st, sc);
+  cudaFreeAsync(sc.small, st);
+  cudaFreeAsync(sc.vec, st);
+  cudaFreeAsync(sc.part, st);
+  cudaFreeAsync(sc.stat, st);
+  cudaFreeAsync(sc.dZ, st);
+  cudaFreeAsync(sc.dY, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess && status == SPAND_OK) status = SPAND_ERR_CUDA;
+  return status;
+}
+
+
+// ------------------------------------------------------------------ no-allocation variant
+// Same solve as sstep_gmres_solve, for callers that must not allocate device
+// memory while they run: for example a host program that hands all device
+// memory to its own pool allocator at start-up, or one that runs under a fixed
+// device-memory budget and cannot afford an allocation failing in mid-solve.
+// Its scratch (basis vectors, Gram partial sums, small dense work, pointer
+// tables) lives in one fixed file-scope device array instead.
+namespace spand {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;   // 8 MiB on every GPU that loads the library
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Device address of the scratch array on the current device.  Host code may
+// not use g_noalloc_scratch directly: its name there is a host-side stand-in.
+int noalloc_base(unsigned char** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SPAND_ERR_CUDA;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return SPAND_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SPAND_ERR_CUDA;
+    g_noalloc_addr[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+  return SPAND_OK;
+}
+
+}  // namespace
+}  // namespace spand
+
+extern "C" int sstep_gmres_solve_noalloc(const bsr_matrix* A, spand_factor_t M, const double* b, double* x,
+                                         const gmres_opts* opts, gmres_stats* stats, cudaStream_t st) {
+  using namespace spand;
+  const int v = gmres_validate(A, M, b, x, opts);
+  if (v != SPAND_OK) return v;
+  const int64_t N = (int64_t)A->K * A->B;
+  const GmresSizes zs = gmres_sizes(opts->restart, opts->s);
+  const size_t b_small = align256(zs.small_tot * sizeof(double));
+  const size_t b_vec = align256(zs.nvec * (size_t)N * sizeof(double));
+  const size_t b_part = align256(zs.part * sizeof(double));
+  const size_t b_stat = align256(4 * sizeof(int));
+  const size_t b_z = align256(zs.maxptr * sizeof(double*));
+  const size_t b_y = align256(64 * sizeof(double*));
+  if (b_small + b_vec + b_part + b_stat + b_z + b_y > kNoAllocScratchBytes) return SPAND_ERR_SCRATCH;
+  unsigned char* base = nullptr;
+  const int sb = noalloc_base(&base);
+  if (sb != SPAND_OK) return sb;
+  GmresScratch sc;
+  unsigned char* p = base;
+  sc.small = reinterpret_cast<double*>(p);
+  p += b_small;
+  sc.vec = reinterpret_cast<double*>(p);
+  p += b_vec;
+  sc.part = reinterpret_cast<double*>(p);
+  p += b_part;
+  sc.stat = reinterpret_cast<int*>(p);
+  p += b_stat;
+  sc.dZ = reinterpret_cast<const double**>(p);
+  p += b_z;
+  sc.dY = reinterpret_cast<const double**>(p);
+  // sstep_core clears the small-matrix and status words it needs zeroed; the
+  // vectors and partial sums are always written before they are read.
+  return sstep_core(A, M, b, x, opts, stats, st, sc);
+}
+
+extern "C" size_t sstep_gmres_noalloc_capacity(void) { return spand::kNoAllocScratchBytes; }
