@@ -13,6 +13,7 @@
 //     rank-revealing QR of Eq. 11) and the explicit Q_c it defines;
 //   * block copies / transposed copies / identity fills for gathers and merges.
 #pragma once
+#include <cooperative_groups.h>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -60,7 +61,8 @@ struct CopyTile {
 
 template <typename T>
 struct QrTask {
-  T* W;              // n x c column-major, ld = n; reflectors stored below the diagonal
+  T* W;              // n x c ROW-major (element (i, j) at i*c + j); overwritten
+  T* V;              // n x min(n,c) column-major: reflector k in column k, rows k..n-1 (v_k[k] = 1)
   T* tau;            // min(n, c)
   T* norm2;          // c scratch
   T* Q;              // explicit Q_c output (n x r, ld = n)
@@ -638,6 +640,173 @@ __global__ void __launch_bounds__(256) k_form_q(const QrTask<T>* tasks) {
       for (int i = k + lane; i < n; i += 32) col[i] -= dot * ((i == k) ? (T)1 : vk[i]);
     }
     __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ RRQR, cluster version
+// Column-pivoted Householder QR of W (n x c, row-major) by a cluster of QR_CS
+// CTAs that split the columns into contiguous chunks.  Each step: every CTA
+// proposes its best remaining column (largest residual norm, lowest index on
+// ties); the proposals are exchanged through distributed shared memory; the
+// owner of the winner builds the Householder vector and the others copy it;
+// every CTA updates its own remaining columns and their norms.  Columns are
+// not moved: a used flag (norm set to -1) replaces the swap, which leaves the
+// reflectors and hence Q unchanged.  The factorization stops at the first k
+// with |R_kk| <= eps |R_00| (or R_00 = 0); columns whose initial norm is
+// already <= eps |R_00| can never be chosen before that and are dropped.
+constexpr int QR_CS = 8;
+constexpr int QR_THREADS = 512;
+
+template <typename T>
+__global__ void __launch_bounds__(QR_THREADS) k_qrcp_cluster(const QrTask<T>* tasks, T eps) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ unsigned char qr_smem2[];
+  T* v = reinterpret_cast<T*>(qr_smem2);           // n: current reflector (local copy)
+  __shared__ T cand_v;
+  __shared__ int cand_i;
+  __shared__ T red_v[32];
+  __shared__ int red_i[32];
+  __shared__ T s_scal[4];                          // [0] tau, [1] beta, [2] nrm0
+  const int q = (int)cluster.block_rank();
+  const QrTask<T> tk = tasks[blockIdx.x / QR_CS];
+  const int n = tk.n, c = tk.c;
+  const int chunk = (c + QR_CS - 1) / QR_CS;
+  const int j0 = min(c, q * chunk), j1 = min(c, j0 + chunk);
+  T* W = tk.W;
+  const size_t ldw = (size_t)c;
+  const int tid = threadIdx.x;
+  // initial column norms of the own chunk
+  for (int j = j0 + tid; j < j1; j += blockDim.x) {
+    T s = 0;
+    for (int i = 0; i < n; ++i) {
+      const T a = W[(size_t)i * ldw + j];
+      s += a * a;
+    }
+    tk.norm2[j] = s;
+  }
+  __syncthreads();
+  const int kmax = min(n, c);
+  int rank = kmax;
+  T nrm0 = 0;
+  for (int k = 0; k < kmax; ++k) {
+    // ---- local proposal
+    T best = -1;
+    int bi = c;
+    for (int j = j0 + tid; j < j1; j += blockDim.x) argmax_pair(best, bi, tk.norm2[j], j);
+    block_argmax(best, bi, red_v, red_i);
+    if (tid == 0) {
+      cand_v = best;
+      cand_i = bi;
+    }
+    cluster.sync();
+    // ---- cluster-wide winner (identical in every CTA)
+    T gbest = -1;
+    int gi = c;
+    for (int r = 0; r < QR_CS; ++r) {
+      const T* rv = cluster.map_shared_rank(&cand_v, r);
+      const int* ri = cluster.map_shared_rank(&cand_i, r);
+      argmax_pair(gbest, gi, *rv, *ri);
+    }
+    const T nrm = sqrt(fmax(gbest, (T)0));
+    if (k == 0) {
+      nrm0 = nrm;
+      // drop columns that can never be chosen before the stopping test
+      const T cut = eps * nrm0;
+      for (int j = j0 + tid; j < j1; j += blockDim.x)
+        if (tk.norm2[j] >= 0 && sqrt(tk.norm2[j]) <= cut) tk.norm2[j] = -1;
+    }
+    const bool stop = (nrm0 == (T)0) || nrm <= eps * nrm0 || gi >= c;
+    if (stop) {
+      rank = k;
+      break;
+    }
+    const int p = gi;
+    const bool owner = (p >= j0 && p < j1);
+    if (owner) {
+      // Householder vector of column p, rows k..n-1
+      T part = 0;
+      for (int i = k + 1 + tid; i < n; i += blockDim.x) {
+        const T a = W[(size_t)i * ldw + p];
+        part += a * a;
+      }
+      const T sigma = block_sum(part, red_v);
+      const T alpha = W[(size_t)k * ldw + p];
+      T tau = 0, beta = alpha, scale = 0;
+      if (sigma > (T)0) {
+        beta = -copysign(sqrt(alpha * alpha + sigma), alpha);
+        tau = (beta - alpha) / beta;
+        scale = (T)1 / (alpha - beta);
+      }
+      for (int i = k + tid; i < n; i += blockDim.x) {
+        const T vi = (i == k) ? (T)1 : W[(size_t)i * ldw + p] * scale;
+        v[i] = vi;
+        tk.V[(size_t)i + (size_t)k * n] = vi;
+      }
+      if (tid == 0) {
+        s_scal[0] = tau;
+        tk.tau[k] = tau;
+        tk.norm2[p] = -1;                  // used
+      }
+    }
+    cluster.sync();
+    // ---- copy the reflector from the owner
+    const int orank = p / chunk;
+    if (!owner) {
+      const T* rv = cluster.map_shared_rank(v, orank);
+      for (int i = k + tid; i < n; i += blockDim.x) v[i] = rv[i];
+      if (tid == 0) s_scal[0] = *cluster.map_shared_rank(&s_scal[0], orank);
+    }
+    __syncthreads();
+    const T tau = s_scal[0];
+    // ---- update the own remaining columns and their norms
+    for (int j = j0 + tid; j < j1; j += blockDim.x) {
+      if (tk.norm2[j] < 0) continue;
+      T dot = 0;
+      for (int i = k; i < n; ++i) dot += v[i] * W[(size_t)i * ldw + j];
+      dot *= tau;
+      T s = 0;
+      for (int i = k; i < n; ++i) {
+        const T a = W[(size_t)i * ldw + j] - dot * v[i];
+        W[(size_t)i * ldw + j] = a;
+        if (i > k) s += a * a;
+      }
+      tk.norm2[j] = s;
+    }
+    __syncthreads();
+  }
+  if (q == 0 && tid == 0) *tk.rank = rank;
+  cluster.sync();   // no CTA leaves while another may still read its shared memory
+}
+
+// explicit Q_c = H_0 ... H_{r-1} [I_r; 0] from the reflectors in V; one CTA
+// per interface, a thread per column of Q_c (only columns j >= k change at
+// step k), accumulated row-major in the (no longer needed) W buffer.
+template <typename T>
+__global__ void __launch_bounds__(512) k_form_q_v(const QrTask<T>* tasks) {
+  const QrTask<T> tk = tasks[blockIdx.x];
+  const int n = tk.n, r = *tk.rank;
+  if (r <= 0) return;
+  T* Qr = tk.W;                           // n x r row-major
+  for (size_t idx = threadIdx.x; idx < (size_t)n * r; idx += blockDim.x) {
+    const int i = (int)(idx / r), j = (int)(idx % r);
+    Qr[idx] = (i == j) ? (T)1 : (T)0;
+  }
+  __syncthreads();
+  for (int k = r - 1; k >= 0; --k) {
+    const T tau = tk.tau[k];
+    const T* vk = tk.V + (size_t)k * n;
+    for (int j = k + threadIdx.x; j < r; j += blockDim.x) {
+      T dot = 0;
+      for (int i = k; i < n; ++i) dot += vk[i] * Qr[(size_t)i * r + j];
+      dot *= tau;
+      for (int i = k; i < n; ++i) Qr[(size_t)i * r + j] -= dot * vk[i];
+    }
+    __syncthreads();
+  }
+  for (size_t idx = threadIdx.x; idx < (size_t)n * r; idx += blockDim.x) {
+    const int j = (int)(idx / n), i = (int)(idx % n);
+    tk.Q[idx] = Qr[(size_t)i * r + j];
   }
 }
 

@@ -522,18 +522,20 @@ static int factor_impl(const Plan& P, const bsr_matrix* A, double eps, int preci
       QrTask<T> t;
       t.n = n[s];
       t.c = cs;
-      t.W = tmp.alloc<T>((size_t)n[s] * cs);
+      t.W = tmp.alloc<T>((size_t)n[s] * cs);             // row-major n x c
+      t.V = tmp.alloc<T>((size_t)n[s] * std::min(n[s], cs));
       t.tau = tmp.alloc<T>(std::min(n[s], cs));
       t.norm2 = tmp.alloc<T>(cs);
       t.Q = nullptr;
       t.rank = d_rank + qt.size();
+      // W = [A_sn A_ns^T]; as a column-major c x n array (ld c) it holds W^T
       int off = 0;
       for (int b : nba[s]) {
-        cps.push_back({blk(s, b), t.W + (size_t)off * n[s], n[s], n[s], n[s], n[b], 0});
+        cps.push_back({blk(s, b), t.W + off, n[s], cs, n[b], n[s], 1});
         off += n[b];
       }
       for (int b : nba[s]) {
-        cps.push_back({blk(b, s), t.W + (size_t)off * n[s], n[b], n[s], n[s], n[b], 1});
+        cps.push_back({blk(b, s), t.W + off, n[b], cs, n[b], n[s], 0});
         off += n[b];
       }
       qt.push_back(t);
@@ -548,9 +550,20 @@ static int factor_impl(const Plan& P, const bsr_matrix* A, double eps, int preci
       auto* dq = tmp.upload(qt);
       const size_t sm = (size_t)nmax_qr * sizeof(T);
       if (sm > kGemvSmemMax) return SPAND_ERR_UNSUPPORTED;
-      cudaFuncSetAttribute(k_qrcp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemvSmemMax);
-      k_qrcp<T><<<(unsigned)qt.size(), 256, sm, st>>>(dq, (T)eps);
-      SPAND_CUDA_TRY(cudaGetLastError());
+      cudaFuncSetAttribute(k_qrcp_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemvSmemMax);
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)(qt.size() * QR_CS), 1, 1);
+      cfg.blockDim = dim3(QR_THREADS, 1, 1);
+      cfg.dynamicSmemBytes = sm;
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = QR_CS;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      SPAND_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_qrcp_cluster<T>, (const QrTask<T>*)dq, (T)eps));
       SPAND_CUDA_TRY(cudaMemcpyAsync(rank.data(), d_rank, sizeof(int) * qt.size(), cudaMemcpyDeviceToHost, st));
     }
     int hflags[4];
@@ -576,7 +589,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* A, double eps, int preci
     if (pm.err) return SPAND_ERR_NOMEM;
     if (!qt.empty()) {
       auto* dq = tmp.upload(qt);
-      k_form_q<T><<<(unsigned)qt.size(), 256, 0, st>>>(dq);
+      k_form_q_v<T><<<(unsigned)qt.size(), 512, 0, st>>>(dq);
     }
     // records for the apply
     for (size_t q = 0; q < Fc.size(); ++q) {
