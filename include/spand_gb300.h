@@ -10,8 +10,11 @@
  * Conventions shared by every entry point
  *  - Return value: int status; 0 = SPAND_OK, negative = error (codes below).
  *    On error no output is guaranteed; handles stay valid and must still be
- *    destroyed.  No entry point writes host globals, except the per-device
- *    address cache of sstep_gmres_solve_noalloc (below).
+ *    destroyed.  No entry point keeps results in host globals.  The only
+ *    host-side state that outlives a call is set once and then read: kernel
+ *    attributes (dynamic shared-memory limits), whether the device schedules
+ *    16-CTA clusters, and the per-device address cache of
+ *    sstep_gmres_solve_noalloc (below).
  *  - Pointers documented as "device" must point to device memory owned by the
  *    caller (any allocator); "host" pointers are caller-owned host memory.
  *    Handles (spand_plan_t, spand_factor_t) are owned by the library and are
@@ -104,6 +107,14 @@ int dg_assemble_jacobian(const dg_mesh* mesh, int p, const double* u_hat,
 int bsr_spmv(const bsr_matrix* A, const double* x, double* y, int transpose,
              cudaStream_t stream);
 
+/* out = alpha * u v^T restricted to the block pattern of A: block k of row e
+ * and column col[k] becomes alpha * u[e*B : e*B+B] v[col[k]*B : col[k]*B+B]^T
+ * (column-major, like val).  With u = lambda = A^-T dL/dx and v = x,
+ * alpha = -1 this is dL/dA of the adjoint of x = A^-1 b on A's pattern.
+ * u, v: device FP64 vectors of length K*B; out: device nnzb*B*B doubles. */
+int bsr_pattern_outer(const bsr_matrix* A, const double* u, const double* v, double alpha, double* out,
+                      cudaStream_t stream);
+
 /* ---------------------------------------------------------------- analysis
  * spand_analyze - Sec. 2.2.1 and Sec. 3.3: nested dissection of the
  * n_theta x n_r element grid (root separator = radial lines j = 0 and
@@ -144,6 +155,25 @@ int spand_factor(spand_plan_t plan, const bsr_matrix* A, double eps, int precisi
                  spand_factor_t* out, cudaStream_t stream);
 int spand_factor_destroy(spand_factor_t F);
 
+/* spand_factor_batched - the factorization of spand_factor for nsys
+ * independent systems at once (the paper factors one system; batching is an
+ * execution choice of this library).  plans[q] and A[q] (host array of nsys
+ * matrices, each with its own block size) describe system q.  The systems'
+ * levels are aligned from the bottom (level l of every system with D_q >= l
+ * is processed together) and every phase of a level (batched LU, inverses,
+ * elimination and Schur products, scaling, RRQR, compression, merge) is one
+ * launch over the clusters of all systems, so small systems fill the GPU
+ * together.  out[q] receives a handle for system q: spand_apply,
+ * spand_factor_stats and sstep_gmres_solve on it act on system q alone (its
+ * own apply program, captured in its own CUDA graph).  The handles share one
+ * factorization; its device memory is released when the last of them is
+ * destroyed.  Handles of different systems may be applied concurrently
+ * (their sweeps touch disjoint memory).  Stats of a handle hold the system's
+ * ranks, root size and apply bytes; phase times and flops are those of the
+ * whole batch.  Errors: as spand_factor (no handle is returned on error). */
+int spand_factor_batched(int nsys, const spand_plan_t* plans, const bsr_matrix* A, double eps,
+                         int precision, spand_factor_t* out, cudaStream_t stream);
+
 typedef struct {
   int levels;               /* D + 1                                          */
   int64_t n_sparsified[32]; /* interfaces sparsified at level l               */
@@ -153,6 +183,16 @@ typedef struct {
   int64_t top_size;         /* size of the last (root) interior               */
   int64_t factor_bytes;     /* device bytes one spand_apply streams (both sweeps) */
   double factor_flops;      /* algorithmic flops of the factorization         */
+  /* Live CUDA-event timings of the factorization on its stream (ms), with
+   * the algorithmic work of the timed kernels: the rank-revealing QRs
+   * (bytes: the trailing block of W read and written once per pivot step)
+   * and the elimination products Y, X and Schur updates (flops 2mnk).      */
+  double t_rrqr_ms;
+  double rrqr_bytes;
+  int rrqr_launches;
+  double t_elim_gemm_ms;
+  double elim_gemm_flops;
+  int elim_gemm_launches;
 } spand_stats;
 int spand_factor_stats(spand_factor_t F, spand_stats* st);
 
@@ -201,6 +241,20 @@ typedef struct {
 
 int sstep_gmres_solve(const bsr_matrix* A, spand_factor_t M, const double* b, double* x,
                       const gmres_opts* opts, gmres_stats* stats, cudaStream_t stream);
+
+/* sstep_gmres_solve_batched - nsys independent solves of sstep_gmres_solve
+ * (host arrays of nsys: A, M (NULL or per-system handles, e.g. from
+ * spand_factor_batched), b, x (device vectors), opts, stats, status).  Each
+ * system runs on its own stream, ordered after `stream`; `stream` is ordered
+ * after all of them on return, and the host has waited for every solve.  A
+ * pool of up to 16 host threads drives the systems so their host round trips
+ * (one per s-block) overlap other systems' kernels.  status[q] is system q's
+ * own status; the return value is SPAND_OK or the first failing status in
+ * system order (argument errors are checked for all systems before any work
+ * is queued).  Not part of the paper: an execution choice of this library. */
+int sstep_gmres_solve_batched(int nsys, const bsr_matrix* A, const spand_factor_t* M,
+                              const double* const* b, double* const* x, const gmres_opts* opts,
+                              gmres_stats* stats, int* status, cudaStream_t stream);
 
 /* sstep_gmres_solve_noalloc - the same solve as sstep_gmres_solve (same
  * arguments, same results), for callers that must not allocate device memory

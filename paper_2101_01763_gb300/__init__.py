@@ -1,7 +1,9 @@
 """GB300 (sm_103a) spaND + s-step GMRES for the DG Newton-step linear solve.
 
 Public API (all compute in the CUDA library libspand_gb300.so):
-    assemble, spmv, Plan, Factor, sstep_gmres, SpandSolve
+    assemble, spmv, Plan, Factor, sstep_gmres, SpandSolve,
+    factor_batched, sstep_gmres_batched (many independent systems)
 """
-from .api import BSR, Factor, Plan, assemble, parse_table, spmv, sstep_gmres  # noqa: F401
+from .api import (BSR, Factor, Plan, SpandSolve, assemble, factor_batched, parse_table,  # noqa: F401
+                  pattern_outer, spmv, sstep_gmres, sstep_gmres_batched)
 from ._lib import SpandError  # noqa: F401

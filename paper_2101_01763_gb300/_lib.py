@@ -41,7 +41,9 @@ class BsrMatrix(C.Structure):
 class SpandStats(C.Structure):
     _fields_ = [("levels", C.c_int), ("n_sparsified", C.c_int64 * 32), ("sum_n", C.c_int64 * 32),
                 ("sum_r", C.c_int64 * 32), ("max_r", C.c_int64 * 32), ("top_size", C.c_int64),
-                ("factor_bytes", C.c_int64), ("factor_flops", C.c_double)]
+                ("factor_bytes", C.c_int64), ("factor_flops", C.c_double),
+                ("t_rrqr_ms", C.c_double), ("rrqr_bytes", C.c_double), ("rrqr_launches", C.c_int),
+                ("t_elim_gemm_ms", C.c_double), ("elim_gemm_flops", C.c_double), ("elim_gemm_launches", C.c_int)]
 
 
 class GmresOpts(C.Structure):
@@ -61,6 +63,8 @@ EXPORTS = {
     "dg_assemble_jacobian": ([C.POINTER(DgMesh), C.c_int, C.c_void_p, C.POINTER(DgFlow), C.c_void_p,
                               C.POINTER(BsrMatrix), C.POINTER(C.c_double), C.c_void_p], C.c_int),
     "bsr_spmv": ([C.POINTER(BsrMatrix), C.c_void_p, C.c_void_p, C.c_int, C.c_void_p], C.c_int),
+    "bsr_pattern_outer": ([C.POINTER(BsrMatrix), C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p],
+                          C.c_int),
     "spand_analyze": ([C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p)], C.c_int),
     "spand_plan_destroy": ([C.c_void_p], C.c_int),
     "spand_plan_sizes": ([C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
@@ -68,11 +72,16 @@ EXPORTS = {
     "spand_plan_export": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "spand_factor": ([C.c_void_p, C.POINTER(BsrMatrix), C.c_double, C.c_int, C.POINTER(C.c_void_p),
                       C.c_void_p], C.c_int),
+    "spand_factor_batched": ([C.c_int, C.POINTER(C.c_void_p), C.POINTER(BsrMatrix), C.c_double, C.c_int,
+                              C.POINTER(C.c_void_p), C.c_void_p], C.c_int),
     "spand_factor_destroy": ([C.c_void_p], C.c_int),
     "spand_factor_stats": ([C.c_void_p, C.POINTER(SpandStats)], C.c_int),
     "spand_apply": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p], C.c_int),
     "sstep_gmres_solve": ([C.POINTER(BsrMatrix), C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(GmresOpts),
                            C.POINTER(GmresStats), C.c_void_p], C.c_int),
+    "sstep_gmres_solve_batched": ([C.c_int, C.POINTER(BsrMatrix), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                   C.POINTER(C.c_void_p), C.POINTER(GmresOpts), C.POINTER(GmresStats),
+                                   C.POINTER(C.c_int), C.c_void_p], C.c_int),
     "sstep_gmres_solve_noalloc": ([C.POINTER(BsrMatrix), C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.POINTER(GmresOpts), C.POINTER(GmresStats), C.c_void_p], C.c_int),
     "sstep_gmres_noalloc_capacity": ([], C.c_size_t),

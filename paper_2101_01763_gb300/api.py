@@ -144,6 +144,12 @@ class Factor:
         self.N = A.K * A.B
         self.precision = precision
 
+    @classmethod
+    def _wrap(cls, h, N, precision):
+        f = cls.__new__(cls)
+        f.h, f.N, f.precision = h, N, precision
+        return f
+
     def apply(self, r, transpose=False, out=None, stream=None):
         _need(r, torch.float64, "r")
         z = torch.empty_like(r) if out is None else out
@@ -156,7 +162,10 @@ class Factor:
         n = s.levels
         return dict(levels=n, n_sparsified=list(s.n_sparsified[:n]), sum_n=list(s.sum_n[:n]),
                     sum_r=list(s.sum_r[:n]), max_r=list(s.max_r[:n]), top_size=s.top_size,
-                    factor_bytes=s.factor_bytes, factor_flops=s.factor_flops)
+                    factor_bytes=s.factor_bytes, factor_flops=s.factor_flops,
+                    t_rrqr_ms=s.t_rrqr_ms, rrqr_bytes=s.rrqr_bytes, rrqr_launches=s.rrqr_launches,
+                    t_elim_gemm_ms=s.t_elim_gemm_ms, elim_gemm_flops=s.elim_gemm_flops,
+                    elim_gemm_launches=s.elim_gemm_launches)
 
     def close(self):
         if getattr(self, "h", None):
@@ -168,6 +177,42 @@ class Factor:
             self.close()
         except Exception:
             pass
+
+
+def factor_batched(plans, As, eps, precision="mixed", stream=None):
+    """spand_factor_batched: one factorization of several systems; a Factor per system."""
+    n = len(As)
+    prec = L.SPAND_FP64 if precision == "fp64" else L.SPAND_MIXED
+    ph = (C.c_void_p * n)(*[p.h.value for p in plans])
+    mats = (L.BsrMatrix * n)(*[A.struct() for A in As])
+    out = (C.c_void_p * n)()
+    L.check(L.lib().spand_factor_batched(n, ph, mats, float(eps), prec, out, _stream(stream)),
+            "spand_factor_batched")
+    return [Factor._wrap(C.c_void_p(out[q]), As[q].K * As[q].B, precision) for q in range(n)]
+
+
+def sstep_gmres_batched(As, Ms, bs, s=4, restart=60, tol=1e-8, max_iters=400, basis="newton", transpose=False,
+                        stream=None):
+    """sstep_gmres_solve_batched: returns (xs, stats list, statuses)."""
+    n = len(As)
+    for b in bs:
+        _need(b, torch.float64, "b")
+    xs = [torch.zeros_like(b) for b in bs]
+    mats = (L.BsrMatrix * n)(*[A.struct() for A in As])
+    mh = (C.c_void_p * n)(*[(M.h.value if M is not None else None) for M in Ms]) if Ms is not None else None
+    bp = (C.c_void_p * n)(*[b.data_ptr() for b in bs])
+    xp = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+    opt = L.GmresOpts(s, restart, tol, max_iters, L.BASIS_NEWTON if basis == "newton" else L.BASIS_MONOMIAL,
+                      int(transpose))
+    opts = (L.GmresOpts * n)(*[opt for _ in range(n)])
+    stt = (L.GmresStats * n)()
+    status = (C.c_int * n)()
+    rc = L.lib().sstep_gmres_solve_batched(n, mats, mh, bp, xp, opts, stt, status, _stream(stream))
+    if rc != L.OK and rc != -6:
+        L.check(rc, "sstep_gmres_solve_batched")
+    stats = [dict(iters=t.iters, restarts=t.restarts, true_relres=t.true_relres, converged=(status[q] == L.OK))
+             for q, t in enumerate(stt)]
+    return xs, stats, list(status)
 
 
 def sstep_gmres(A, M, b, x0=None, s=4, restart=40, tol=1e-8, max_iters=400, basis="newton",
@@ -188,3 +233,45 @@ def sstep_gmres(A, M, b, x0=None, s=4, restart=40, tol=1e-8, max_iters=400, basi
                  shifts=[complex(stt.shifts_re[k], stt.shifts_im[k]) for k in range(s)],
                  converged=(status == L.OK))
     return x, stats
+
+
+def pattern_outer(A, u, v, alpha=1.0, out=None, stream=None):
+    """bsr_pattern_outer: alpha * u v^T on A's block pattern (values in A's layout)."""
+    _need(u, torch.float64, "u")
+    _need(v, torch.float64, "v")
+    o = torch.empty_like(A.val) if out is None else out
+    st = A.struct()
+    L.check(L.lib().bsr_pattern_outer(C.byref(st), _ptr(u), _ptr(v), float(alpha), _ptr(o), _stream(stream)),
+            "bsr_pattern_outer")
+    return o
+
+
+class SpandSolve(torch.autograd.Function):
+    """x = A^-1 b by spaND-preconditioned s-step GMRES, differentiable in (A values, b).
+
+    backward: lambda = A^-T g by s-step GMRES with the transposed spaND apply
+    (the factor of the forward solve is reused), dL/db = lambda and
+    dL/dA = -lambda x^T on A's block pattern (bsr_pattern_outer).
+    Call as SpandSolve.apply(val, b, A, plan, eps, precision, s, restart, tol).
+    """
+
+    @staticmethod
+    def forward(ctx, val, b, A, plan, eps=1e-3, precision="fp64", s=4, restart=60, tol=1e-10):
+        A2 = BSR(A.K, A.B, A.row_ptr, A.col, val.detach().contiguous())
+        F = Factor(plan, A2, eps, precision)
+        x, st = sstep_gmres(A2, F, b.detach().contiguous(), s=s, restart=restart, tol=tol)
+        if not st["converged"]:
+            raise L.SpandError(-6, "SpandSolve.forward")
+        ctx.A, ctx.F, ctx.opts = A2, F, (s, restart, tol)
+        ctx.save_for_backward(x)
+        return x
+
+    @staticmethod
+    def backward(ctx, g):
+        (x,) = ctx.saved_tensors
+        s, restart, tol = ctx.opts
+        lam, st = sstep_gmres(ctx.A, ctx.F, g.contiguous(), s=s, restart=restart, tol=tol, transpose=True)
+        if not st["converged"]:
+            raise L.SpandError(-6, "SpandSolve.backward")
+        dval = pattern_outer(ctx.A, lam, x, alpha=-1.0)
+        return dval, lam, None, None, None, None, None, None, None

@@ -220,6 +220,76 @@ int build_plan(int n_theta, int n_r, int B, int D, Plan& P) {
   return SPAND_OK;
 }
 
+int build_union_plan(const std::vector<const Plan*>& ps, Plan& U) {
+  if (ps.empty()) return SPAND_ERR_ARG;
+  U = Plan();
+  U.nsys = (int)ps.size();
+  int64_t dof = 0;
+  int64_t K = 0;
+  for (const Plan* p : ps) {
+    if (!p || p->lv.size() != (size_t)p->D + 1) return SPAND_ERR_ARG;
+    U.sys_elem0.push_back((int)K);
+    U.sys_dof0.push_back(dof);
+    U.sys_K.push_back(p->K);
+    U.sys_B.push_back(p->B);
+    U.sys_D.push_back(p->D);
+    K += p->K;
+    dof += (int64_t)p->K * p->B;
+    U.D = std::max(U.D, p->D);
+  }
+  if (K > INT32_MAX || dof > INT32_MAX) return SPAND_ERR_UNSUPPORTED;
+  U.K = (int)K;
+  U.B = ps[0]->B;
+  for (const Plan* p : ps)
+    if (p->B != U.B) U.B = 0;   // mixed block sizes: per-system sys_B
+  U.lv.resize(U.D + 1);
+  U.sys_of.resize(U.D + 1);
+  // per level: offset of each system's clusters and surviving clusters
+  std::vector<std::vector<int>> c_off(U.D + 2, std::vector<int>(ps.size(), 0));
+  std::vector<std::vector<int>> s_off(U.D + 2, std::vector<int>(ps.size(), 0));
+  for (int l = 0; l <= U.D; ++l) {
+    int cc = 0, sc = 0;
+    for (size_t s = 0; s < ps.size(); ++s) {
+      c_off[l][s] = cc;
+      s_off[l][s] = sc;
+      if (l <= ps[s]->D) {
+        cc += (int)ps[s]->lv[l].cl.size();
+        sc += (int)ps[s]->lv[l].surv.size();
+      }
+    }
+  }
+  int node0 = 0;
+  std::vector<int> node_off(ps.size());
+  for (size_t s = 0; s < ps.size(); ++s) {
+    node_off[s] = node0;
+    node0 += (int)ps[s]->depth.size();
+  }
+  for (int l = 0; l <= U.D; ++l) {
+    LevelInfo& L = U.lv[l];
+    for (size_t s = 0; s < ps.size(); ++s) {
+      if (l > ps[s]->D) continue;
+      const LevelInfo& Ls = ps[s]->lv[l];
+      const int co = c_off[l][s];
+      for (const Cluster& c : Ls.cl) {
+        Cluster u = c;
+        u.node = c.node + node_off[s];
+        for (int& e : u.elems) e += U.sys_elem0[s];
+        for (int& ch : u.children) ch += s_off[l > 0 ? l - 1 : 0][s];
+        L.cl.push_back(std::move(u));
+        U.sys_of[l].push_back((int)s);
+      }
+      for (int v : Ls.surv) L.surv.push_back(v + co);
+      for (auto& pr : Ls.pattern) L.pattern.push_back({pr.first + co, pr.second + co});
+      for (auto& pr : Ls.after) L.after.push_back({pr.first + co, pr.second + co});
+      for (int v : Ls.parent) {
+        if (l + 1 > ps[s]->D) return SPAND_ERR_ARG;
+        L.parent.push_back(v + c_off[l + 1][s]);
+      }
+    }
+  }
+  return SPAND_OK;
+}
+
 void level0_positions(const Plan& P, std::vector<int>& cl_of, std::vector<int>& pos_in) {
   cl_of.assign(P.K, -1);
   pos_in.assign(P.K, -1);

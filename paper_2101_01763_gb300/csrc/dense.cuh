@@ -42,7 +42,16 @@ struct GemmTerm {
   const T* A;
   const T* B;
   int lda, ldb, k, ta, tb;
+  int tri;           // 1: op(A) lower triangular, 2: op(B) upper triangular (zero k-chunks skipped)
 };
+
+// number of k values of term t that can be non-zero for the output tile at (i0, j0)
+template <typename T>
+__device__ inline int term_klim(const GemmTerm<T>& tm, int i0, int j0, int BM, int BN) {
+  if (tm.tri == 1) return min(tm.k, i0 + BM);
+  if (tm.tri == 2) return min(tm.k, j0 + BN);
+  return tm.k;
+}
 
 struct TileItem {
   int task, tm, tn;
@@ -201,19 +210,129 @@ __global__ void __launch_bounds__(256) k_getrf_panel(const MatRef<T>* mats, int 
   }
 }
 
-// permutation from LAPACK-style interchanges: (P^T b)[k] = b[perm[k]]
+// Same contract as k_getrf_panel, with the panel (rows k0..n-1 of the 32 panel
+// columns) staged in shared memory: pivot search, interchanges, scaling and the
+// rank-1 updates run on-chip; afterwards the panel is written back, its row
+// interchanges are applied to the columns outside the panel, and U12 =
+// L11^-1 A12 is formed.  Used when (n - k0) * 32 values fit the shared budget.
+constexpr int LU_SMEM_BYTES = 160 * 1024;
+
 template <typename T>
-__global__ void k_ipiv_to_perm(const MatRef<T>* mats, int nmat) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_getrf_panel_smem(const MatRef<T>* mats, int nmat, int k0, int* flags) {
+  extern __shared__ unsigned char lu_smem[];
+  T* P = reinterpret_cast<T*>(lu_smem);          // panel, column-major m x jb (ld m)
+  __shared__ T sv[32];
+  __shared__ int si[32];
+  __shared__ T L11[LU_NB][LU_NB + 1];
+  __shared__ int piv_loc[LU_NB];
+  const int b = blockIdx.x;
   if (b >= nmat) return;
   const MatRef<T> M = mats[b];
-  for (int k = 0; k < M.n; ++k) M.perm[k] = k;
-  for (int k = 0; k < M.n; ++k) {
-    int p = M.ipiv[k];
-    int t = M.perm[k];
-    M.perm[k] = M.perm[p];
-    M.perm[p] = t;
+  const int n = M.n;
+  if (k0 >= n) return;
+  T* A = M.A;
+  const size_t ld = n;
+  const int jb = min(LU_NB, n - k0), m = n - k0;
+  if ((size_t)m * jb * sizeof(T) > (size_t)LU_SMEM_BYTES) return;   // host routes these elsewhere
+  for (int idx = threadIdx.x; idx < m * jb; idx += blockDim.x) {
+    const int r = idx % m, c = idx / m;
+    P[idx] = A[(k0 + r) + (size_t)(k0 + c) * ld];
   }
+  __syncthreads();
+  for (int j = 0; j < jb; ++j) {
+    T best = -1;
+    int bi = m;
+    for (int i = j + threadIdx.x; i < m; i += blockDim.x) {
+      T a = fabs(P[i + j * m]);
+      if (a != a) a = (T)INFINITY;
+      argmax_pair(best, bi, a, i);
+    }
+    block_argmax(best, bi, sv, si);
+    const int p = bi;
+    if (threadIdx.x == 0) {
+      M.ipiv[k0 + j] = k0 + p;
+      piv_loc[j] = p;
+    }
+    if (p != j && threadIdx.x < jb) {
+      const int c = threadIdx.x;
+      const T t = P[j + c * m];
+      P[j + c * m] = P[p + c * m];
+      P[p + c * m] = t;
+    }
+    __syncthreads();
+    const T pv = P[j + j * m];
+    if (!(pv == pv) || isinf(pv)) {
+      if (threadIdx.x == 0) atomicOr(flags, 2);
+    } else if (pv == (T)0) {
+      if (threadIdx.x == 0) atomicOr(flags, 1);
+    } else {
+      for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
+        const T l = P[i + j * m] / pv;
+        P[i + j * m] = l;
+        for (int c = j + 1; c < jb; ++c) P[i + c * m] -= l * P[j + c * m];
+      }
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < m * jb; idx += blockDim.x) {
+    const int r = idx % m, c = idx / m;
+    A[(k0 + r) + (size_t)(k0 + c) * ld] = P[idx];
+  }
+  // row interchanges on the columns outside the panel: a thread per column
+  for (int c = threadIdx.x; c < n - jb; c += blockDim.x) {
+    const int col = (c < k0) ? c : c + jb;
+    T* colp = A + (size_t)col * ld + k0;
+    for (int j = 0; j < jb; ++j) {
+      const int p = piv_loc[j];
+      if (p != j) {
+        const T t = colp[j];
+        colp[j] = colp[p];
+        colp[p] = t;
+      }
+    }
+  }
+  for (int t = threadIdx.x; t < jb * jb; t += blockDim.x) {
+    const int r = t % jb, c = t / jb;
+    L11[r][c] = P[r + c * m];
+  }
+  __syncthreads();
+  for (int c = k0 + jb + threadIdx.x; c < n; c += blockDim.x) {
+    T x[LU_NB];
+    T* col = A + (size_t)c * ld + k0;
+#pragma unroll
+    for (int r = 0; r < LU_NB; ++r) x[r] = (r < jb) ? col[r] : (T)0;
+#pragma unroll
+    for (int r = 1; r < LU_NB; ++r) {
+      T s = x[r];
+#pragma unroll
+      for (int q = 0; q < r; ++q) s -= L11[r][q] * x[q];
+      x[r] = s;
+    }
+#pragma unroll
+    for (int r = 0; r < LU_NB; ++r)
+      if (r < jb) col[r] = x[r];
+  }
+}
+
+// permutation from LAPACK-style interchanges: (P^T b)[k] = b[perm[k]];
+// one CTA per matrix, the sequential swaps run in shared memory
+template <typename T>
+__global__ void k_ipiv_to_perm(const MatRef<T>* mats, int nmat) {
+  extern __shared__ int pm_s[];
+  const int b = blockIdx.x;
+  if (b >= nmat) return;
+  const MatRef<T> M = mats[b];
+  for (int k = threadIdx.x; k < M.n; k += blockDim.x) pm_s[k] = k;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int k = 0; k < M.n; ++k) {
+      const int p = M.ipiv[k];
+      const int t = pm_s[k];
+      pm_s[k] = pm_s[p];
+      pm_s[p] = t;
+    }
+  __syncthreads();
+  for (int k = threadIdx.x; k < M.n; k += blockDim.x) M.perm[k] = pm_s[k];
 }
 
 // ------------------------------------------------------------------ grouped GEMM
@@ -245,7 +364,8 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask<T>* tasks, const Ge
     for (int c = 0; c < 4; ++c) acc[r][c] = 0;
   for (int t = tk.t0; t < tk.t1; ++t) {
     const GemmTerm<T> tm = terms[t];
-    for (int l0 = 0; l0 < tm.k; l0 += BK) {
+    const int klim = term_klim(tm, i0, j0, BM, BN);
+    for (int l0 = 0; l0 < klim; l0 += BK) {
       for (int idx = threadIdx.x; idx < BM * BK; idx += 256) {
         int i, l;
         if (!tm.ta) { i = idx % BM; l = idx / BM; }
@@ -296,6 +416,160 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask<T>* tasks, const Ge
       *cp = v;
     }
   }
+}
+
+// ------------------------------------------------------------------ grouped GEMM, FP32 on tensor cores
+// Same task/term/tile contract as k_gemm<float>.  128 threads = 4 warps, a
+// 64 x 64 output tile, each warp a 32 x 32 sub-tile of m16n8k8 TF32 MMAs with
+// FP32 accumulation.  SPLIT = 3: error-compensated 3xTF32 (each operand split
+// into a TF32 high part and a TF32 remainder; hi*hi + hi*lo + lo*hi), which
+// keeps the products at about FP32 accuracy; SPLIT = 1: plain TF32.
+__device__ inline uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ inline void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ inline void cp_async4(void* smem, const void* g, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int sz = valid ? 4 : 0;                      // 0 bytes read -> zero fill
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(g), "r"(sz));
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ inline void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+template <int SPLIT>
+__global__ void __launch_bounds__(128) k_gemm_tc(const GemmTask<float>* tasks, const GemmTerm<float>* terms,
+                                                 const TileItem* tiles) {
+  constexpr int BM = 64, BN = 64, BK = 32, PAD = 8;
+  __shared__ float As[2][BK][BM + PAD];   // k-major: As[s][l][i] = op(A)[i0+i, l0+l]
+  __shared__ float Bs[2][BK][BN + PAD];   // Bs[s][l][j] = op(B)[l0+l, j0+j]
+  const TileItem it = tiles[blockIdx.x];
+  const GemmTask<float> tk = tasks[it.task];
+  const int i0 = it.tm * BM, j0 = it.tn * BN;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  const int g = lane >> 2, t4 = lane & 3;
+  float acc[2][4][4];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+  // flattened (term, k-chunk) sequence
+  int cur_t = tk.t0, cur_l = 0;
+  auto advance = [&](int& t, int& l) {
+    l += BK;
+    while (t < tk.t1 && l >= term_klim(terms[t], i0, j0, BM, BN)) {
+      ++t;
+      l = 0;
+    }
+  };
+  while (cur_t < tk.t1 && term_klim(terms[cur_t], i0, j0, BM, BN) <= 0) ++cur_t;
+  auto issue = [&](int stage, int t, int l0) {
+    const GemmTerm<float> tm = terms[t];
+    for (int idx = threadIdx.x; idx < BM * BK; idx += 128) {
+      int i, l;
+      if (!tm.ta) { i = idx % BM; l = idx / BM; }
+      else { l = idx % BK; i = idx / BK; }
+      const int gi = i0 + i, gl = l0 + l;
+      const bool ok = gi < tk.m && gl < tm.k;
+      const float* src = ok ? (tm.ta ? tm.A + gl + (size_t)gi * tm.lda : tm.A + gi + (size_t)gl * tm.lda) : tm.A;
+      cp_async4(&As[stage][l][i], src, ok);
+    }
+    for (int idx = threadIdx.x; idx < BN * BK; idx += 128) {
+      int j, l;
+      if (!tm.tb) { l = idx % BK; j = idx / BK; }
+      else { j = idx % BN; l = idx / BN; }
+      const int gj = j0 + j, gl = l0 + l;
+      const bool ok = gj < tk.n && gl < tm.k;
+      const float* src = ok ? (tm.tb ? tm.B + gj + (size_t)gl * tm.ldb : tm.B + gl + (size_t)gj * tm.ldb) : tm.B;
+      cp_async4(&Bs[stage][l][j], src, ok);
+    }
+  };
+  int stage = 0;
+  if (cur_t < tk.t1) issue(0, cur_t, cur_l);
+  cp_async_commit();
+  while (cur_t < tk.t1) {
+    int nt = cur_t, nl = cur_l;
+    advance(nt, nl);
+    if (nt < tk.t1) issue(stage ^ 1, nt, nl);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; kk += 8) {
+      uint32_t ah[2][4], al[2][4], bh[4][2], bl[4][2];
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const int r = wm + a * 16 + g;
+        const float x0 = As[stage][kk + t4][r], x1 = As[stage][kk + t4][r + 8];
+        const float x2 = As[stage][kk + t4 + 4][r], x3 = As[stage][kk + t4 + 4][r + 8];
+        ah[a][0] = to_tf32(x0);
+        ah[a][1] = to_tf32(x1);
+        ah[a][2] = to_tf32(x2);
+        ah[a][3] = to_tf32(x3);
+        if (SPLIT == 3) {
+          al[a][0] = to_tf32(x0 - __uint_as_float(ah[a][0]));
+          al[a][1] = to_tf32(x1 - __uint_as_float(ah[a][1]));
+          al[a][2] = to_tf32(x2 - __uint_as_float(ah[a][2]));
+          al[a][3] = to_tf32(x3 - __uint_as_float(ah[a][3]));
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int cidx = wn + b * 8 + g;
+        const float y0 = Bs[stage][kk + t4][cidx], y1 = Bs[stage][kk + t4 + 4][cidx];
+        bh[b][0] = to_tf32(y0);
+        bh[b][1] = to_tf32(y1);
+        if (SPLIT == 3) {
+          bl[b][0] = to_tf32(y0 - __uint_as_float(bh[b][0]));
+          bl[b][1] = to_tf32(y1 - __uint_as_float(bh[b][1]));
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          if (SPLIT == 3) {
+            mma_tf32(acc[a][b], al[a], bh[b]);
+            mma_tf32(acc[a][b], ah[a], bl[b]);
+          }
+          mma_tf32(acc[a][b], ah[a], bh[b]);
+        }
+    }
+    __syncthreads();
+    stage ^= 1;
+    cur_t = nt;
+    cur_l = nl;
+  }
+  cp_async_wait<0>();
+  // epilogue: c0 (g, 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1)
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int gi = i0 + wm + a * 16 + g + ((e >= 2) ? 8 : 0);
+        const int gj = j0 + wn + b * 8 + 2 * t4 + (e & 1);
+        if (gi < tk.m && gj < tk.n) {
+          float* cp = tk.C + gi + (size_t)gj * tk.ldc;
+          float v = tk.alpha * acc[a][b][e];
+          if (tk.beta != 0.f) v += tk.beta * *cp;
+          *cp = v;
+        }
+      }
 }
 
 // ------------------------------------------------------------------ triangular inverses
@@ -447,6 +721,75 @@ __global__ void __launch_bounds__(256) k_inv_upper(const InvTask<T>* tasks, cons
     }
     __syncthreads();
     if (r0 == 0) break;
+  }
+}
+
+// Inverse of one 32 x 32 diagonal block of the LU factors: lower = unit lower
+// L (strict lower part of LU), upper = U (upper part of LU).  One warp per
+// block, a lane per column; the block of the output is overwritten.
+template <typename T>
+struct DiagInvTask {
+  const T* LU;
+  T* out;
+  int n, p, lower;   // block p covers rows/cols [32p, min(n, 32p+32))
+};
+
+template <typename T>
+__global__ void __launch_bounds__(32) k_inv_diag(const DiagInvTask<T>* tasks) {
+  __shared__ T Bl[32][33];
+  const DiagInvTask<T> tk = tasks[blockIdx.x];
+  const int n = tk.n, o = 32 * tk.p, b = min(32, n - o);
+  const int c = threadIdx.x;
+  for (int r = 0; r < 32; ++r) Bl[r][c] = (r < b && c < b) ? tk.LU[(o + r) + (size_t)(o + c) * n] : (T)0;
+  __syncwarp();
+  if (c < b) {
+    T x[32];
+    if (tk.lower) {
+#pragma unroll
+      for (int r = 0; r < 32; ++r) x[r] = (r == c) ? (T)1 : (T)0;
+#pragma unroll
+      for (int r = 1; r < 32; ++r) {
+        T s = x[r];
+#pragma unroll
+        for (int q = 0; q < r; ++q) s -= Bl[r][q] * x[q];
+        x[r] = (r < b) ? s : (T)0;
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < 32; ++r) x[r] = (r == c) ? (T)1 : (T)0;
+#pragma unroll
+      for (int r = 31; r >= 0; --r) {
+        T s = x[r];
+#pragma unroll
+        for (int q = r + 1; q < 32; ++q) s -= Bl[r][q] * x[q];
+        x[r] = (r < b) ? s / Bl[r][r] : (T)0;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 32; ++r)
+      if (r < b) tk.out[(o + r) + (size_t)(o + c) * n] = x[r];
+  }
+}
+
+// zero a batch of n x n matrices
+template <typename T>
+__global__ void k_zero_mats(T* const* ptr, const int* nn) {
+  T* p = ptr[blockIdx.y];
+  const size_t tot = (size_t)nn[blockIdx.y] * nn[blockIdx.y];
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < tot; i += (size_t)gridDim.x * blockDim.x)
+    p[i] = (T)0;
+}
+
+// columns of out scaled by dscale[j]  (U^-1 |d|^1/2)
+template <typename T>
+__global__ void k_scale_cols(const InvTask<T>* tasks, const InvTile* tiles) {
+  const InvTile tl = tiles[blockIdx.x];
+  const InvTask<T> tk = tasks[tl.task];
+  if (!tk.dscale) return;
+  const int n = tk.n, jb = min(32, n - tl.j0);
+  for (int idx = threadIdx.x; idx < n * jb; idx += blockDim.x) {
+    const int r = idx % n, c = tl.j0 + idx / n;
+    tk.out[r + (size_t)c * n] *= tk.dscale[c];
   }
 }
 
@@ -657,8 +1000,14 @@ __global__ void __launch_bounds__(256) k_form_q(const QrTask<T>* tasks) {
 constexpr int QR_CS = 8;
 constexpr int QR_THREADS = 512;
 
-template <typename T>
-__global__ void __launch_bounds__(QR_THREADS) k_qrcp_cluster(const QrTask<T>* tasks, T eps) {
+// SMEM = true: each CTA keeps its column chunk of W (n x chunk, row-major) in
+// shared memory for the whole factorization (dynamic shared memory holds the
+// reflector, then the chunk); SMEM = false: W stays in global memory.
+// Threads are laid out as (row segment, column): a group of CW consecutive
+// columns is processed by all NT/CW row segments, so narrow chunks still keep
+// every thread busy; partial dots and norms are combined in shared memory.
+template <typename T, bool SMEM, int CS, int NT>
+__global__ void __launch_bounds__(NT, 1) k_qrcp_cluster(const QrTask<T>* tasks, T eps) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ unsigned char qr_smem2[];
@@ -667,25 +1016,55 @@ __global__ void __launch_bounds__(QR_THREADS) k_qrcp_cluster(const QrTask<T>* ta
   __shared__ int cand_i;
   __shared__ T red_v[32];
   __shared__ int red_i[32];
-  __shared__ T s_scal[4];                          // [0] tau, [1] beta, [2] nrm0
+  __shared__ T allc_v[CS];
+  __shared__ int allc_i[CS];
+  __shared__ T s_scal[4];                          // [0] tau, [1] winner norm^2
+  __shared__ int s_win;
+  __shared__ T part[NT];                           // (segment, column) partials
+  __shared__ T dotv[NT];
   const int q = (int)cluster.block_rank();
-  const QrTask<T> tk = tasks[blockIdx.x / QR_CS];
+  const QrTask<T> tk = tasks[blockIdx.x / CS];
   const int n = tk.n, c = tk.c;
-  const int chunk = (c + QR_CS - 1) / QR_CS;
+  const int chunk = (c + CS - 1) / CS;
   const int j0 = min(c, q * chunk), j1 = min(c, j0 + chunk);
-  T* W = tk.W;
-  const size_t ldw = (size_t)c;
   const int tid = threadIdx.x;
-  // initial column norms of the own chunk
-  for (int j = j0 + tid; j < j1; j += blockDim.x) {
-    T s = 0;
-    for (int i = 0; i < n; ++i) {
-      const T a = W[(size_t)i * ldw + j];
-      s += a * a;
+  const int wdt = j1 - j0;
+  const int CW = max(32, min(NT, (wdt + 31) / 32 * 32));   // columns per group
+  const int SEG = NT / CW;                                   // row segments
+  const int cl = tid % CW, seg = tid / CW;
+  const bool in_grid = seg < SEG;
+  T* Wg = tk.W;
+  T* Ws = v + ((n + 31) & ~31);
+  const size_t ldg = (size_t)c;
+  auto at = [&](int i, int j) -> T& {
+    if (SMEM) return Ws[(size_t)i * chunk + (j - j0)];
+    return Wg[(size_t)i * ldg + j];
+  };
+  if (SMEM) {
+    for (int idx = tid; idx < n * wdt; idx += NT) {
+      const int i = idx / wdt, jj = idx % wdt;
+      Ws[(size_t)i * chunk + jj] = Wg[(size_t)i * ldg + j0 + jj];
     }
-    tk.norm2[j] = s;
+    __syncthreads();
   }
-  __syncthreads();
+  // ---- initial column norms
+  for (int g = j0; g < j1; g += CW) {
+    const int j = g + cl;
+    T s = 0;
+    if (in_grid && j < j1)
+      for (int i = seg; i < n; i += SEG) {
+        const T a = at(i, j);
+        s += a * a;
+      }
+    part[tid] = s;
+    __syncthreads();
+    if (seg == 0 && j < j1) {
+      T t = 0;
+      for (int r = 0; r < SEG; ++r) t += part[r * CW + cl];
+      tk.norm2[j] = t;
+    }
+    __syncthreads();
+  }
   const int kmax = min(n, c);
   int rank = kmax;
   T nrm0 = 0;
@@ -693,27 +1072,34 @@ __global__ void __launch_bounds__(QR_THREADS) k_qrcp_cluster(const QrTask<T>* ta
     // ---- local proposal
     T best = -1;
     int bi = c;
-    for (int j = j0 + tid; j < j1; j += blockDim.x) argmax_pair(best, bi, tk.norm2[j], j);
+    for (int j = j0 + tid; j < j1; j += NT) argmax_pair(best, bi, tk.norm2[j], j);
     block_argmax(best, bi, red_v, red_i);
     if (tid == 0) {
       cand_v = best;
       cand_i = bi;
     }
     cluster.sync();
-    // ---- cluster-wide winner (identical in every CTA)
-    T gbest = -1;
-    int gi = c;
-    for (int r = 0; r < QR_CS; ++r) {
-      const T* rv = cluster.map_shared_rank(&cand_v, r);
-      const int* ri = cluster.map_shared_rank(&cand_i, r);
-      argmax_pair(gbest, gi, *rv, *ri);
+    // ---- cluster-wide winner: one remote read per thread, in parallel
+    if (tid < CS) {
+      allc_v[tid] = *cluster.map_shared_rank(&cand_v, tid);
+      allc_i[tid] = *cluster.map_shared_rank(&cand_i, tid);
     }
-    const T nrm = sqrt(fmax(gbest, (T)0));
+    __syncthreads();
+    if (tid == 0) {
+      T gb = -1;
+      int gi = c;
+      for (int r = 0; r < CS; ++r) argmax_pair(gb, gi, allc_v[r], allc_i[r]);
+      s_scal[1] = gb;
+      s_win = gi;
+    }
+    __syncthreads();
+    const int gi = s_win;
+    const T nrm = sqrt(fmax(s_scal[1], (T)0));
     if (k == 0) {
       nrm0 = nrm;
       // drop columns that can never be chosen before the stopping test
       const T cut = eps * nrm0;
-      for (int j = j0 + tid; j < j1; j += blockDim.x)
+      for (int j = j0 + tid; j < j1; j += NT)
         if (tk.norm2[j] >= 0 && sqrt(tk.norm2[j]) <= cut) tk.norm2[j] = -1;
     }
     const bool stop = (nrm0 == (T)0) || nrm <= eps * nrm0 || gi >= c;
@@ -725,21 +1111,21 @@ __global__ void __launch_bounds__(QR_THREADS) k_qrcp_cluster(const QrTask<T>* ta
     const bool owner = (p >= j0 && p < j1);
     if (owner) {
       // Householder vector of column p, rows k..n-1
-      T part = 0;
-      for (int i = k + 1 + tid; i < n; i += blockDim.x) {
-        const T a = W[(size_t)i * ldw + p];
-        part += a * a;
+      T prt = 0;
+      for (int i = k + 1 + tid; i < n; i += NT) {
+        const T a = at(i, p);
+        prt += a * a;
       }
-      const T sigma = block_sum(part, red_v);
-      const T alpha = W[(size_t)k * ldw + p];
-      T tau = 0, beta = alpha, scale = 0;
+      const T sigma = block_sum(prt, red_v);
+      const T alpha = at(k, p);
+      T tau = 2, beta = -alpha, scale = 0;          // column already reduced: H = I - 2 e_k e_k^T
       if (sigma > (T)0) {
         beta = -copysign(sqrt(alpha * alpha + sigma), alpha);
         tau = (beta - alpha) / beta;
         scale = (T)1 / (alpha - beta);
       }
-      for (int i = k + tid; i < n; i += blockDim.x) {
-        const T vi = (i == k) ? (T)1 : W[(size_t)i * ldw + p] * scale;
+      for (int i = k + tid; i < n; i += NT) {
+        const T vi = (i == k) ? (T)1 : at(i, p) * scale;
         v[i] = vi;
         tk.V[(size_t)i + (size_t)k * n] = vi;
       }
@@ -754,59 +1140,90 @@ __global__ void __launch_bounds__(QR_THREADS) k_qrcp_cluster(const QrTask<T>* ta
     const int orank = p / chunk;
     if (!owner) {
       const T* rv = cluster.map_shared_rank(v, orank);
-      for (int i = k + tid; i < n; i += blockDim.x) v[i] = rv[i];
+      for (int i = k + tid; i < n; i += NT) v[i] = rv[i];
       if (tid == 0) s_scal[0] = *cluster.map_shared_rank(&s_scal[0], orank);
     }
     __syncthreads();
     const T tau = s_scal[0];
     // ---- update the own remaining columns and their norms
-    for (int j = j0 + tid; j < j1; j += blockDim.x) {
-      if (tk.norm2[j] < 0) continue;
-      T dot = 0;
-      for (int i = k; i < n; ++i) dot += v[i] * W[(size_t)i * ldw + j];
-      dot *= tau;
-      T s = 0;
-      for (int i = k; i < n; ++i) {
-        const T a = W[(size_t)i * ldw + j] - dot * v[i];
-        W[(size_t)i * ldw + j] = a;
-        if (i > k) s += a * a;
+    for (int g = j0; g < j1; g += CW) {
+      const int j = g + cl;
+      const bool act = in_grid && j < j1 && tk.norm2[j] >= 0;
+      T d0 = 0, d1 = 0;
+      if (act) {
+        int i = k + seg;
+        for (; i + SEG < n; i += 2 * SEG) {
+          d0 += v[i] * at(i, j);
+          d1 += v[i + SEG] * at(i + SEG, j);
+        }
+        if (i < n) d0 += v[i] * at(i, j);
       }
-      tk.norm2[j] = s;
+      part[tid] = d0 + d1;
+      __syncthreads();
+      if (seg == 0) {
+        T t = 0;
+        for (int r = 0; r < SEG; ++r) t += part[r * CW + cl];
+        dotv[cl] = t * tau;
+      }
+      __syncthreads();
+      T s0 = 0;
+      if (act) {
+        const T dt = dotv[cl];
+        int i = k + seg;
+        for (; i + SEG < n; i += 2 * SEG) {
+          T& a = at(i, j);
+          T& b = at(i + SEG, j);
+          a -= dt * v[i];
+          b -= dt * v[i + SEG];
+          if (i > k) s0 += a * a;
+          s0 += b * b;
+        }
+        if (i < n) {
+          T& a = at(i, j);
+          a -= dt * v[i];
+          if (i > k) s0 += a * a;
+        }
+      }
+      part[tid] = s0;
+      __syncthreads();
+      if (seg == 0 && j < j1 && tk.norm2[j] >= 0) {
+        T t = 0;
+        for (int r = 0; r < SEG; ++r) t += part[r * CW + cl];
+        tk.norm2[j] = t;
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
   if (q == 0 && tid == 0) *tk.rank = rank;
   cluster.sync();   // no CTA leaves while another may still read its shared memory
 }
 
-// explicit Q_c = H_0 ... H_{r-1} [I_r; 0] from the reflectors in V; one CTA
-// per interface, a thread per column of Q_c (only columns j >= k change at
-// step k), accumulated row-major in the (no longer needed) W buffer.
+// bytes of dynamic shared memory the SMEM variant needs for an n x c problem
 template <typename T>
-__global__ void __launch_bounds__(512) k_form_q_v(const QrTask<T>* tasks) {
-  const QrTask<T> tk = tasks[blockIdx.x];
-  const int n = tk.n, r = *tk.rank;
-  if (r <= 0) return;
-  T* Qr = tk.W;                           // n x r row-major
-  for (size_t idx = threadIdx.x; idx < (size_t)n * r; idx += blockDim.x) {
-    const int i = (int)(idx / r), j = (int)(idx % r);
-    Qr[idx] = (i == j) ? (T)1 : (T)0;
-  }
-  __syncthreads();
-  for (int k = r - 1; k >= 0; --k) {
-    const T tau = tk.tau[k];
-    const T* vk = tk.V + (size_t)k * n;
-    for (int j = k + threadIdx.x; j < r; j += blockDim.x) {
-      T dot = 0;
-      for (int i = k; i < n; ++i) dot += vk[i] * Qr[(size_t)i * r + j];
-      dot *= tau;
-      for (int i = k; i < n; ++i) Qr[(size_t)i * r + j] -= dot * vk[i];
-    }
-    __syncthreads();
-  }
-  for (size_t idx = threadIdx.x; idx < (size_t)n * r; idx += blockDim.x) {
-    const int j = (int)(idx / n), i = (int)(idx % n);
-    tk.Q[idx] = Qr[(size_t)i * r + j];
+inline size_t qrcp_smem_bytes(int n, int c, int cs) {
+  const size_t chunk = (size_t)(c + cs - 1) / cs;
+  return (((size_t)n + 31) & ~(size_t)31) * sizeof(T) + (size_t)n * chunk * sizeof(T);
+}
+
+// compact-WY form of the explicit Q_c = H_0 ... H_{r-1} [I_r; 0] = [I_r; 0] - V T V_top^T,
+// with T upper triangular and T^-1 = striu(V^T V) + diag(1/tau) (Householder
+// reflectors, tau = 2 / v^T v).  This kernel turns the Gram G = V^T V (r x r,
+// ld r) into T^-1 in place: diagonal 1/tau, strictly lower part zero.
+template <typename T>
+struct WyTask {
+  T* G;
+  const T* tau;
+  int r;
+};
+
+template <typename T>
+__global__ void k_wy_tinv(const WyTask<T>* tasks) {
+  const WyTask<T> tk = tasks[blockIdx.x];
+  const int r = tk.r;
+  for (int idx = threadIdx.x; idx < r * r; idx += blockDim.x) {
+    const int i = idx % r, j = idx / r;
+    if (i == j) tk.G[idx] = (T)1 / tk.tau[i];
+    else if (i > j) tk.G[idx] = 0;
   }
 }
 

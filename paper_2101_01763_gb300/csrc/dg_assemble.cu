@@ -490,6 +490,7 @@ extern "C" int dg_assemble_jacobian(const dg_mesh* mesh, int p, const double* u_
       face_point(f, T.tq[k], xi, eta);
       basis_at(p, xi, eta, T.fpsi[f][k], nullptr, nullptr);
     }
+  if (spand::set_dyn_smem((const void*)k_assemble, sizeof(Smem)) < (long long)sizeof(Smem)) return SPAND_ERR_UNSUPPORTED;
   double* d_scr = nullptr;  // [0] = dtau, [1] = bad flag (as int)
   SPAND_CUDA_TRY(cudaMallocAsync(&d_scr, 2 * sizeof(double), stream));
   const double big = 1e300;
@@ -498,7 +499,6 @@ extern "C" int dg_assemble_jacobian(const dg_mesh* mesh, int p, const double* u_
   int* d_bad = reinterpret_cast<int*>(d_scr + 1);
   k_time_step<<<(K + 127) / 128, 128, 0, stream>>>(mesh->nodes, nt, nr, p, u_hat, fl, d_scr, d_bad, T);
   const size_t smem = sizeof(Smem);
-  cudaFuncSetAttribute(k_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_assemble<<<K, 256, smem, stream>>>(mesh->nodes, nt, nr, p, u_hat, fl, d_scr, A->row_ptr, rhs,
                                        A->val, d_bad, T);
   SPAND_CUDA_TRY(cudaGetLastError());

@@ -17,7 +17,9 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <atomic>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -828,23 +830,89 @@ extern "C" int sstep_gmres_solve(const bsr_matrix* A, spand_factor_t M, const do
   const int64_t N = (int64_t)A->K * A->B;
   const GmresSizes zs = gmres_sizes(m, s);
   GmresScratch sc{};
-  if (cudaMallocAsync(&sc.small, zs.small_tot * sizeof(double), st) != cudaSuccess) return SPAND_ERR_NOMEM;
-  if (cudaMallocAsync(&sc.vec, zs.nvec * N * sizeof(double), st) != cudaSuccess) return SPAND_ERR_NOMEM;
-  if (cudaMallocAsync(&sc.part, zs.part * sizeof(double), st) != cudaSuccess) return SPAND_ERR_NOMEM;
-  if (cudaMallocAsync(&sc.stat, 4 * sizeof(int), st) != cudaSuccess) return SPAND_ERR_NOMEM;
-  if (cudaMallocAsync((void**)&sc.dZ, zs.maxptr * sizeof(double*), st) != cudaSuccess) return SPAND_ERR_NOMEM;
-  if (cudaMallocAsync((void**)&sc.dY, 64 * sizeof(double*), st) != cudaSuccess) return SPAND_ERR_NOMEM;
+  auto release = [&] {
+    for (void* p : {(void*)sc.small, (void*)sc.vec, (void*)sc.part, (void*)sc.stat, (void*)sc.dZ, (void*)sc.dY})
+      if (p) cudaFreeAsync(p, st);
+  };
+  if (cudaMallocAsync(&sc.small, zs.small_tot * sizeof(double), st) != cudaSuccess ||
+      cudaMallocAsync(&sc.vec, zs.nvec * N * sizeof(double), st) != cudaSuccess ||
+      cudaMallocAsync(&sc.part, zs.part * sizeof(double), st) != cudaSuccess ||
+      cudaMallocAsync(&sc.stat, 4 * sizeof(int), st) != cudaSuccess ||
+      cudaMallocAsync((void**)&sc.dZ, zs.maxptr * sizeof(double*), st) != cudaSuccess ||
+      cudaMallocAsync((void**)&sc.dY, 64 * sizeof(double*), st) != cudaSuccess) {
+    cudaGetLastError();
+    release();
+    return SPAND_ERR_NOMEM;
+  }
   int status = sstep_core(A, M, b, x, opts, stats, st, sc);
-  cudaFreeAsync(sc.small, st);
-  cudaFreeAsync(sc.vec, st);
-  cudaFreeAsync(sc.part, st);
-  cudaFreeAsync(sc.stat, st);
-  cudaFreeAsync(sc.dZ, st);
-  cudaFreeAsync(sc.dY, st);
+  release();
   if (cudaStreamSynchronize(st) != cudaSuccess && status == SPAND_OK) status = SPAND_ERR_CUDA;
   return status;
 }
 
+
+// ------------------------------------------------------------------ batched solve
+// Independent systems solved concurrently: each on its own stream (ordered
+// after the caller's stream by an event, and the caller's stream after all of
+// them), driven by a small pool of host threads, so that one system's host
+// round trips overlap the others' kernels.
+extern "C" int sstep_gmres_solve_batched(int nsys, const bsr_matrix* A, const spand_factor_t* M,
+                                         const double* const* b, double* const* x, const gmres_opts* opts,
+                                         gmres_stats* stats, int* status, cudaStream_t st) {
+  using namespace spand;
+  if (nsys <= 0 || !A || !b || !x || !opts || !stats || !status) return SPAND_ERR_ARG;
+  for (int q = 0; q < nsys; ++q) {
+    status[q] = SPAND_ERR_ARG;
+    const int v = gmres_validate(&A[q], M ? M[q] : nullptr, b[q], x[q], &opts[q]);
+    if (v != SPAND_OK) return v;
+  }
+  int dev = 0;
+  SPAND_CUDA_TRY(cudaGetDevice(&dev));
+  std::vector<cudaStream_t> ss(nsys, nullptr);
+  std::vector<cudaEvent_t> done(nsys, nullptr);
+  cudaEvent_t start = nullptr;
+  auto cleanup = [&] {
+    for (int q = 0; q < nsys; ++q) {
+      if (done[q]) cudaEventDestroy(done[q]);
+      if (ss[q]) cudaStreamDestroy(ss[q]);
+    }
+    if (start) cudaEventDestroy(start);
+  };
+  int rc = SPAND_OK;
+  if (cudaEventCreateWithFlags(&start, cudaEventDisableTiming) != cudaSuccess) rc = SPAND_ERR_CUDA;
+  for (int q = 0; q < nsys && rc == SPAND_OK; ++q)
+    if (cudaStreamCreateWithFlags(&ss[q], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&done[q], cudaEventDisableTiming) != cudaSuccess)
+      rc = SPAND_ERR_CUDA;
+  if (rc == SPAND_OK && cudaEventRecord(start, st) != cudaSuccess) rc = SPAND_ERR_CUDA;
+  for (int q = 0; q < nsys && rc == SPAND_OK; ++q)
+    if (cudaStreamWaitEvent(ss[q], start, 0) != cudaSuccess) rc = SPAND_ERR_CUDA;
+  if (rc != SPAND_OK) {
+    cudaGetLastError();
+    cleanup();
+    return rc;
+  }
+  std::atomic<int> next{0};
+  auto worker = [&] {
+    cudaSetDevice(dev);
+    for (int q = next++; q < nsys; q = next++)
+      status[q] = sstep_gmres_solve(&A[q], M ? M[q] : nullptr, b[q], x[q], &opts[q], &stats[q], ss[q]);
+  };
+  const int nthr = std::max(1, std::min(nsys, 16));
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nthr; ++t) pool.emplace_back(worker);
+  worker();
+  for (auto& th : pool) th.join();
+  for (int q = 0; q < nsys; ++q) {
+    if (cudaEventRecord(done[q], ss[q]) != cudaSuccess || cudaStreamWaitEvent(st, done[q], 0) != cudaSuccess)
+      rc = SPAND_ERR_CUDA;
+  }
+  cleanup();
+  if (rc != SPAND_OK) return rc;
+  for (int q = 0; q < nsys; ++q)
+    if (status[q] != SPAND_OK) return status[q];
+  return SPAND_OK;
+}
 
 // ------------------------------------------------------------------ no-allocation variant
 // Same solve as sstep_gmres_solve, for callers that must not allocate device

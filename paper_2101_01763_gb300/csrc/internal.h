@@ -1,5 +1,6 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
+#include <atomic>
 #include <cstdint>
 #include <map>
 #include <string>
@@ -10,10 +11,17 @@
 
 namespace spand {
 
+// With SPAND_DEBUG=1 in the environment, a failing CUDA call is reported on
+// stderr with its source location and the runtime's error string.
+void report_cuda_error(cudaError_t e, const char* expr, const char* file, int line);
+
 #define SPAND_CUDA_TRY(call)                                   \
   do {                                                         \
     cudaError_t e__ = (call);                                  \
-    if (e__ != cudaSuccess) return SPAND_ERR_CUDA;             \
+    if (e__ != cudaSuccess) {                                  \
+      spand::report_cuda_error(e__, #call, __FILE__, __LINE__); \
+      return SPAND_ERR_CUDA;                                   \
+    }                                                          \
   } while (0)
 
 #define SPAND_TRY(call)              \
@@ -21,6 +29,44 @@ namespace spand {
     int s__ = (call);                \
     if (s__ != SPAND_OK) return s__; \
   } while (0)
+
+// Runs f() once per device of the calling thread (kernel attributes are
+// per-device settings); setting them twice from two threads is harmless.
+template <typename F>
+inline void once_per_device(std::atomic<uint64_t>& done, F f) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    f();
+    return;
+  }
+  const uint64_t bit = uint64_t(1) << dev;
+  if (done.load(std::memory_order_acquire) & bit) return;
+  f();
+  done.fetch_or(bit, std::memory_order_release);
+}
+
+// Sets the kernel's dynamic shared-memory limit to min(want, opt-in limit of
+// the device - the kernel's static shared memory) and returns the value set,
+// or -1 when a query fails.  A failing runtime call here is cleared, so it
+// cannot surface later as the error of an unrelated launch.
+inline long long set_dyn_smem(const void* func, size_t want) {
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, func) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  long long v = (long long)optin - (long long)fa.sharedSizeBytes;
+  if ((long long)want < v) v = (long long)want;
+  if (v < 0) return -1;
+  if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return v;
+}
 
 // ----------------------------------------------------------------- analysis
 struct Cluster {
@@ -45,9 +91,21 @@ struct Plan {
   std::vector<std::vector<int>> node_elems;
   std::vector<int> owner;
   std::vector<LevelInfo> lv;  // D + 1 levels
+  // Disjoint union of several systems (batched factorization).  Levels are
+  // aligned from the bottom (level l of every system with D_s >= l forms
+  // union level l); a system whose top level D_s < D has no clusters above
+  // it.  For one system: nsys = 1, sys_of empty, sys_* hold that system.
+  int nsys = 1;
+  std::vector<std::vector<int>> sys_of;   // per level: cluster -> system
+  std::vector<int> sys_elem0, sys_K, sys_B, sys_D;
+  std::vector<int64_t> sys_dof0;          // first unknown of each system
+  int64_t n_dof() const { return sys_dof0.empty() ? (int64_t)K * B : sys_dof0.back() + (int64_t)sys_K.back() * sys_B.back(); }
+  int system_of(int l, int c) const { return sys_of.empty() ? 0 : sys_of[l][c]; }
 };
 
 int build_plan(int n_theta, int n_r, int B, int D, Plan& P);
+// union of the given plans (each keeps its own block size)
+int build_union_plan(const std::vector<const Plan*>& ps, Plan& U);
 
 // position of element e inside its level-0 cluster and that cluster's index
 void level0_positions(const Plan& P, std::vector<int>& cl_of, std::vector<int>& pos_in);

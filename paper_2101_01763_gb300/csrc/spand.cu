@@ -14,10 +14,13 @@
 // a fixed list of gather-GEMV launches built once per factorization.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "dense.cuh"
@@ -28,8 +31,19 @@ namespace spand {
 
 // largest dynamic shared memory any kernel here asks for (x vectors, reflectors)
 constexpr size_t kGemvSmemMax = 200 * 1024;
+// dynamic shared memory of the RRQR cluster kernel (W chunk + reflector)
+constexpr size_t kQrSmemMax = 212 * 1024;   // + <= 9 KB static stays under 227 KB
 
 // ------------------------------------------------------------------ device memory
+void report_cuda_error(cudaError_t e, const char* expr, const char* file, int line) {
+  static const bool on = [] {
+    const char* v = std::getenv("SPAND_DEBUG");
+    return v && v[0] == '1';
+  }();
+  if (on) std::fprintf(stderr, "spand: %s:%d: %s -> %s (%s)\n", file, line, expr, cudaGetErrorName(e),
+                       cudaGetErrorString(e));
+}
+
 struct DevMem {
   std::vector<void*> ptrs;
   cudaStream_t st = nullptr;
@@ -73,7 +87,10 @@ static void launch_gemm(DevMem& tmp, const std::vector<GemmTask<T>>& tasks, cons
   auto* dm = tmp.upload(terms);
   auto* dl = tmp.upload(tiles);
   if (tmp.err) return;
-  k_gemm<T><<<(unsigned)tiles.size(), 256, 0, st>>>(dt, dm, dl);
+  if constexpr (std::is_same<T, float>::value)
+    k_gemm_tc<3><<<(unsigned)tiles.size(), 128, 0, st>>>(dt, dm, dl);   // FP32 factors: 3xTF32 tensor cores
+  else
+    k_gemm<T><<<(unsigned)tiles.size(), 256, 0, st>>>(dt, dm, dl);
 }
 
 template <typename T>
@@ -128,8 +145,31 @@ static void batched_getrf(DevMem& tmp, std::vector<MatRef<T>>& mats, int* d_flag
   for (auto& m : mats) nmax = std::max(nmax, m.n);
   auto* dm = tmp.upload(mats);
   if (tmp.err) return;
+  // matrices whose panels fit the shared-memory budget take the staged kernel
+  std::vector<MatRef<T>> small, large;
+  int nsmall_max = 0;
+  for (auto& m : mats) {
+    if ((size_t)m.n * LU_NB * sizeof(T) <= (size_t)LU_SMEM_BYTES) {
+      small.push_back(m);
+      nsmall_max = std::max(nsmall_max, m.n);
+    } else {
+      large.push_back(m);
+    }
+  }
+  auto* ds = small.empty() ? nullptr : tmp.upload(small);
+  auto* dlg = large.empty() ? nullptr : tmp.upload(large);
+  if (tmp.err) return;
+  static std::atomic<uint64_t> attr{0};
+  once_per_device(attr, [] {
+    set_dyn_smem((const void*)k_getrf_panel_smem<T>, LU_SMEM_BYTES);
+    set_dyn_smem((const void*)k_ipiv_to_perm<T>, 200 * 1024);
+  });
   for (int k0 = 0; k0 < nmax; k0 += LU_NB) {
-    k_getrf_panel<T><<<(unsigned)mats.size(), 256, 0, st>>>(dm, (int)mats.size(), k0, d_flags);
+    if (ds && k0 < nsmall_max) {
+      const size_t sm = (size_t)(nsmall_max - k0) * std::min(LU_NB, nsmall_max - k0) * sizeof(T);
+      k_getrf_panel_smem<T><<<(unsigned)small.size(), 256, sm, st>>>(ds, (int)small.size(), k0, d_flags);
+    }
+    if (dlg) k_getrf_panel<T><<<(unsigned)large.size(), 256, 0, st>>>(dlg, (int)large.size(), k0, d_flags);
     std::vector<GemmTask<T>> tasks;
     std::vector<GemmTerm<T>> terms;
     for (auto& m : mats) {
@@ -143,36 +183,119 @@ static void batched_getrf(DevMem& tmp, std::vector<MatRef<T>>& mats, int* d_flag
     }
     launch_gemm(tmp, tasks, terms, st);
   }
-  k_ipiv_to_perm<T><<<((unsigned)mats.size() + 127) / 128, 128, 0, st>>>(dm, (int)mats.size());
+  k_ipiv_to_perm<T><<<(unsigned)mats.size(), 128, (size_t)nmax * sizeof(int), st>>>(dm, (int)mats.size());
 }
 
 // L^-1 (optionally row-scaled by 1/d) and U^-1 (optionally column-scaled by d)
+// by a bottom-up block recursion on the grouped GEMM: invert the 32 x 32
+// diagonal blocks, then for block sizes 32, 64, 128, ... combine neighbouring
+// blocks,  X21 = -X22 (L21 X11)  and  Y12 = -Y11 (U12 Y22).
 template <typename T>
 static void batched_inverses(DevMem& tmp, const std::vector<MatRef<T>>& mats, const std::vector<T*>& Linv,
                              const std::vector<T*>& Uinv, const std::vector<const T*>& dscale, cudaStream_t st) {
   if (mats.empty()) return;
-  std::vector<InvTask<T>> lt, ut;
-  std::vector<int> ident_max;
-  std::vector<InvTile> tiles;
+  // zero both outputs (the opposite triangles must read as zeros)
+  {
+    std::vector<T*> ptr;
+    std::vector<int> nn;
+    for (size_t b = 0; b < mats.size(); ++b) {
+      ptr.push_back(Linv[b]);
+      nn.push_back(mats[b].n);
+      ptr.push_back(Uinv[b]);
+      nn.push_back(mats[b].n);
+    }
+    auto* dp = tmp.upload(ptr);
+    auto* dn = tmp.upload(nn);
+    if (tmp.err) return;
+    for (size_t off = 0; off < ptr.size(); off += 65535) {
+      const unsigned cnt = (unsigned)std::min<size_t>(65535, ptr.size() - off);
+      k_zero_mats<T><<<dim3(32, cnt), 256, 0, st>>>(dp + off, dn + off);
+    }
+  }
+  std::vector<DiagInvTask<T>> dt;
+  int nmax = 0;
   for (size_t b = 0; b < mats.size(); ++b) {
-    // L^-1 unpermuted: pass the identity placement
+    const int n = mats[b].n;
+    nmax = std::max(nmax, n);
+    for (int p = 0; 32 * p < n; ++p) {
+      dt.push_back({mats[b].A, Linv[b], n, p, 1});
+      dt.push_back({mats[b].A, Uinv[b], n, p, 0});
+    }
+  }
+  if (!dt.empty()) {
+    auto* dd = tmp.upload(dt);
+    if (tmp.err) return;
+    k_inv_diag<T><<<(unsigned)dt.size(), 32, 0, st>>>(dd);
+  }
+  for (int bs = 32; bs < nmax; bs *= 2) {
+    // one scratch array per level for the products L21 X11 and U12 Y22
+    size_t wtot = 0;
+    for (size_t b = 0; b < mats.size(); ++b)
+      for (int a0 = 0; a0 + bs < mats[b].n; a0 += 2 * bs) wtot += 2 * (size_t)bs * std::min(bs, mats[b].n - a0 - bs);
+    if (wtot == 0) continue;
+    T* W = tmp.alloc<T>(wtot);
+    if (tmp.err) return;
+    size_t woff = 0;
+    std::vector<GemmTask<T>> t1, t2;
+    std::vector<GemmTerm<T>> m1, m2;
+    for (size_t b = 0; b < mats.size(); ++b) {
+      const int n = mats[b].n;
+      const T* LU = mats[b].A;
+      for (int a0 = 0; a0 + bs < n; a0 += 2 * bs) {
+        const int c0 = a0 + bs, na = bs, nc = std::min(bs, n - c0);
+        // lower: X21 (nc x na) = -X22 (L21 X11)
+        T* W1 = W + woff;
+        woff += (size_t)nc * na;
+        m1.push_back({LU + c0 + (size_t)a0 * n, Linv[b] + a0 + (size_t)a0 * n, n, n, na, 0, 0, 0});
+        t1.push_back({W1, nc, nc, na, (T)1, (T)0, (int)m1.size() - 1, (int)m1.size()});
+        m2.push_back({Linv[b] + c0 + (size_t)c0 * n, W1, n, nc, nc, 0, 0, 1});   // X22 lower
+        t2.push_back({Linv[b] + c0 + (size_t)a0 * n, n, nc, na, (T)-1, (T)0, (int)m2.size() - 1, (int)m2.size()});
+        // upper: Y12 (na x nc) = -Y11 (U12 Y22)
+        T* W2 = W + woff;
+        woff += (size_t)na * nc;
+        m1.push_back({LU + a0 + (size_t)c0 * n, Uinv[b] + c0 + (size_t)c0 * n, n, n, nc, 0, 0, 2});   // Y22 upper
+        t1.push_back({W2, na, na, nc, (T)1, (T)0, (int)m1.size() - 1, (int)m1.size()});
+        m2.push_back({Uinv[b] + a0 + (size_t)a0 * n, W2, n, na, na, 0, 0, 0});
+        t2.push_back({Uinv[b] + a0 + (size_t)c0 * n, n, na, nc, (T)-1, (T)0, (int)m2.size() - 1, (int)m2.size()});
+      }
+    }
+    launch_gemm(tmp, t1, m1, st);
+    launch_gemm(tmp, t2, m2, st);
+  }
+  // scalings of the interface form: SL = diag(1/d) L^-1, SU = U^-1 diag(d)
+  std::vector<InvTask<T>> lt, ut;
+  std::vector<InvTile> tiles;
+  bool any = false;
+  for (size_t b = 0; b < mats.size(); ++b) {
     lt.push_back({mats[b].A, Linv[b], nullptr, dscale[b], mats[b].n});
     ut.push_back({mats[b].A, Uinv[b], nullptr, dscale[b], mats[b].n});
+    if (dscale[b]) any = true;
     for (int j0 = 0; j0 < mats[b].n; j0 += 32) tiles.push_back({(int)b, j0});
   }
-  int nmax = 0;
-  for (auto& m : mats) nmax = std::max(nmax, m.n);
-  std::vector<int> iota(nmax);
-  for (int i = 0; i < nmax; ++i) iota[i] = i;
-  const int* d_iota = tmp.upload(iota);
-  for (auto& t : lt) t.perm = d_iota;
+  if (!any || tiles.empty()) return;
   auto* dlt = tmp.upload(lt);
   auto* dut = tmp.upload(ut);
   auto* dtl = tmp.upload(tiles);
-  if (tmp.err || tiles.empty()) return;
-  k_inv_lower<T><<<(unsigned)tiles.size(), 256, 0, st>>>(dlt, dtl);
-  k_inv_upper<T><<<(unsigned)tiles.size(), 256, 0, st>>>(dut, dtl);
+  if (tmp.err) return;
   k_scale_rows<T><<<(unsigned)tiles.size(), 256, 0, st>>>(dlt, dtl);
+  k_scale_cols<T><<<(unsigned)tiles.size(), 256, 0, st>>>(dut, dtl);
+}
+
+// U^-1 only (no permutation, no scaling)
+template <typename T>
+static void batched_upper_inverse(DevMem& tmp, const std::vector<MatRef<T>>& mats, const std::vector<T*>& Uinv,
+                                  cudaStream_t st) {
+  if (mats.empty()) return;
+  std::vector<InvTask<T>> ut;
+  std::vector<InvTile> tiles;
+  for (size_t b = 0; b < mats.size(); ++b) {
+    ut.push_back({mats[b].A, Uinv[b], nullptr, nullptr, mats[b].n});
+    for (int j0 = 0; j0 < mats[b].n; j0 += 32) tiles.push_back({(int)b, j0});
+  }
+  auto* dut = tmp.upload(ut);
+  auto* dtl = tmp.upload(tiles);
+  if (tmp.err || tiles.empty()) return;
+  k_inv_upper<T><<<(unsigned)tiles.size(), 256, 0, st>>>(dut, dtl);
 }
 
 // ------------------------------------------------------------------ factor object
@@ -189,13 +312,36 @@ struct ApplyProg {
   std::vector<Phase> tfwd, tbwd;   // M^-T
 };
 
+// apply of one system (or of every system) of a factorization: the unknowns
+// [off, off + N) of the factor's slot space and the sweeps that touch them
+template <typename T>
+struct Program {
+  ApplyProg<T> prog;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int off = 0, N = 0;
+  int64_t bytes = 0;          // factor bytes one apply reads
+  ~Program() {
+    for (int t = 0; t < 2; ++t)
+      if (graph[t]) cudaGraphExecDestroy(graph[t]);
+  }
+};
+
 struct FactorBase {
   virtual ~FactorBase() {}
   int precision = 0;
   int N = 0, D = 0;
   spand_stats stats{};
+  std::vector<spand_stats> sys_stats;   // per system of a batched factorization
   DevMem mem;               // persistent device memory
+  virtual int apply(int prog, const double* r, double* z, int transpose, cudaStream_t st) = 0;
+  virtual int prog_size(int prog) const = 0;
+  virtual int64_t prog_bytes(int prog) const = 0;
 };
+
+template <typename T>
+struct FactorT;
+template <typename T>
+int apply_impl(FactorT<T>* F, Program<T>& pg, const double* r, double* zout, int transpose, cudaStream_t st);
 
 template <typename T>
 struct FactorT : FactorBase {
@@ -203,13 +349,13 @@ struct FactorT : FactorBase {
   T* z = nullptr;
   T* park_b = nullptr;
   T* park_c = nullptr;
-  ApplyProg<T> prog;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  cudaStream_t graph_stream[2] = {nullptr, nullptr};
-  ~FactorT() override {
-    for (int t = 0; t < 2; ++t)
-      if (graph[t]) cudaGraphExecDestroy(graph[t]);
+  // [0]: every system; [1 + q]: system q alone (batched factorizations)
+  std::vector<std::unique_ptr<Program<T>>> progs;
+  int apply(int prog, const double* r, double* zz, int transpose, cudaStream_t st) override {
+    return apply_impl<T>(this, *progs[prog], r, zz, transpose, st);
   }
+  int prog_size(int prog) const override { return progs[prog]->N; }
+  int64_t prog_bytes(int prog) const override { return progs[prog]->bytes; }
 };
 
 // host-side records of one level for building the apply program
@@ -239,9 +385,17 @@ struct LevelRec {
   std::vector<int> n;         // per cluster size
 };
 
-template <typename T>
-__global__ void k_perm_slots(const int* slots, const int* perm, int* out, int n) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = slots[perm[i]];
+struct PermSlotTask {
+  const int* slots;
+  const int* perm;
+  int* out;
+  int n;
+};
+
+// out[i] = slots[perm[i]] for every task (one CTA per task)
+__global__ void k_perm_slots(const PermSlotTask* tasks) {
+  const PermSlotTask tk = tasks[blockIdx.x];
+  for (int i = threadIdx.x; i < tk.n; i += blockDim.x) tk.out[i] = tk.slots[tk.perm[i]];
 }
 
 template <typename T>
@@ -260,10 +414,15 @@ __global__ void k_level0_gather(const double* val, const int* row_of, const int*
 }
 
 template <typename T>
-static int factor_impl(const Plan& P, const bsr_matrix* A, double eps, int precision, FactorT<T>* F,
+static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, int precision, FactorT<T>* F,
                        cudaStream_t st) {
-  const int D = P.D, B = P.B, K = P.K;
-  F->N = K * B;
+  const int D = P.D, K = P.K;
+  const int nsys = P.nsys;
+  auto sysB = [&](int s) { return P.sys_B.empty() ? P.B : P.sys_B[s]; };
+  auto sysE0 = [&](int s) { return P.sys_elem0.empty() ? 0 : P.sys_elem0[s]; };
+  auto sysDof0 = [&](int s) -> int64_t { return P.sys_dof0.empty() ? 0 : P.sys_dof0[s]; };
+  auto sysK = [&](int s) { return P.sys_K.empty() ? P.K : P.sys_K[s]; };
+  F->N = (int)P.n_dof();
   F->D = D;
   F->precision = precision;
   F->mem.st = st;
@@ -271,19 +430,22 @@ static int factor_impl(const Plan& P, const bsr_matrix* A, double eps, int preci
   spand_stats& S = F->stats;
   memset(&S, 0, sizeof(S));
   S.levels = D + 1;
+  F->sys_stats.assign(nsys, spand_stats{});
+  for (int q = 0; q < nsys; ++q) F->sys_stats[q].levels = (P.sys_D.empty() ? D : P.sys_D[q]) + 1;
   int* d_flags = pm.alloc<int>(4);
   if (pm.err) return SPAND_ERR_NOMEM;
   SPAND_CUDA_TRY(cudaMemsetAsync(d_flags, 0, 4 * sizeof(int), st));
 
-  // ---- level-0 sizes, slots, blocks
+  // ---- level-0 sizes, slots, blocks (a cluster never mixes systems)
   std::vector<int> cl_of, pos_in;
   level0_positions(P, cl_of, pos_in);
   std::vector<int> n(P.lv[0].cl.size());
   std::vector<std::vector<int>> slots(n.size());
   for (size_t c = 0; c < n.size(); ++c) {
-    n[c] = (int)P.lv[0].cl[c].elems.size() * B;
+    const int q = P.system_of(0, (int)c), Bq = sysB(q);
+    n[c] = (int)P.lv[0].cl[c].elems.size() * Bq;
     for (int e : P.lv[0].cl[c].elems)
-      for (int d = 0; d < B; ++d) slots[c].push_back(e * B + d);
+      for (int d = 0; d < Bq; ++d) slots[c].push_back((int)(sysDof0(q) + (int64_t)(e - sysE0(q)) * Bq + d));
   }
   // arena of the current level: blocks in pattern U after
   T* arena = nullptr;
@@ -309,36 +471,88 @@ static int factor_impl(const Plan& P, const bsr_matrix* A, double eps, int preci
   DevMem lvmem;  // memory of the current level arena (freed after compression)
   lvmem.st = st;
   SPAND_TRY(layout(P.lv[0], n, lvmem));
-  {
-    // gather the BSR blocks into the level-0 cluster blocks
+  for (int q = 0; q < nsys; ++q) {
+    // gather the BSR blocks of system q into the level-0 cluster blocks
+    const bsr_matrix* A = As[q];
+    const int Kq = sysK(q), Bq = sysB(q), e0 = sysE0(q);
     DevMem tmp;
     tmp.st = st;
-    std::vector<int> rp(K + 1), col(A->nnzb);
-    SPAND_CUDA_TRY(cudaMemcpyAsync(rp.data(), A->row_ptr, sizeof(int) * (K + 1), cudaMemcpyDeviceToHost, st));
+    std::vector<int> rp(Kq + 1), col(A->nnzb);
+    SPAND_CUDA_TRY(cudaMemcpyAsync(rp.data(), A->row_ptr, sizeof(int) * (Kq + 1), cudaMemcpyDeviceToHost, st));
     SPAND_CUDA_TRY(cudaMemcpyAsync(col.data(), A->col, sizeof(int) * A->nnzb, cudaMemcpyDeviceToHost, st));
     SPAND_CUDA_TRY(cudaStreamSynchronize(st));
+    if (rp[0] != 0 || rp[Kq] != A->nnzb) return SPAND_ERR_ARG;
     std::vector<T*> dst(A->nnzb);
     std::vector<int> ldv(A->nnzb);
-    for (int e = 0; e < K; ++e)
+    for (int e = 0; e < Kq; ++e)
       for (int k = rp[e]; k < rp[e + 1]; ++k) {
+        if (k < 0 || k >= A->nnzb || col[k] < 0 || col[k] >= Kq) return SPAND_ERR_ARG;
         const int f = col[k];
-        const int a = cl_of[e], b = cl_of[f];
+        const int a = cl_of[e0 + e], b = cl_of[e0 + f];
         auto it = boff.find({a, b});
         if (it == boff.end()) return SPAND_ERR_ARG;
-        dst[k] = arena + it->second + (size_t)pos_in[e] * B + (size_t)pos_in[f] * B * n[a];
+        dst[k] = arena + it->second + (size_t)pos_in[e0 + e] * Bq + (size_t)pos_in[e0 + f] * Bq * n[a];
         ldv[k] = n[a];
       }
+    if (A->nnzb == 0) continue;
     T* const* d_dst = tmp.upload(dst);
     const int* d_ld = tmp.upload(ldv);
     if (tmp.err) return SPAND_ERR_NOMEM;
-    k_level0_gather<T><<<A->nnzb, 256, 0, st>>>(A->val, nullptr, nullptr, nullptr, nullptr, d_ld, d_dst, A->nnzb, B);
+    k_level0_gather<T><<<A->nnzb, 256, 0, st>>>(A->val, nullptr, nullptr, nullptr, nullptr, d_ld, d_dst, A->nnzb, Bq);
     SPAND_CUDA_TRY(cudaGetLastError());
     tmp.free_all();
   }
 
+  // phase timers (events on the factorization stream): per level RRQR and
+  // elimination-GEMM start/stop; read after each level's synchronisation
+  struct Ev {
+    cudaEvent_t a = nullptr, b = nullptr;
+    bool used = false;
+  };
+  std::vector<Ev> ev_qr(D + 1), ev_gm(D + 1);
+  auto ev_begin = [&](Ev& e) {
+    if (!e.a) {
+      cudaEventCreate(&e.a);
+      cudaEventCreate(&e.b);
+    }
+    cudaEventRecord(e.a, st);
+    e.used = true;
+  };
+  auto ev_end = [&](Ev& e) { cudaEventRecord(e.b, st); };
+  auto ev_read = [&](Ev& e) -> double {
+    float ms = 0.f;
+    if (e.used && cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) return ms;
+    return 0.0;
+  };
+  struct EvGuard {
+    std::vector<Ev>* v[2];
+    ~EvGuard() {
+      for (auto* p : v)
+        for (auto& e : *p) {
+          if (e.a) cudaEventDestroy(e.a);
+          if (e.b) cudaEventDestroy(e.b);
+        }
+    }
+  } ev_guard{{&ev_qr, &ev_gm}};
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+  SPAND_CUDA_TRY(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+  SPAND_CUDA_TRY(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
+  SPAND_CUDA_TRY(cudaEventCreateWithFlags(&join_ev, cudaEventDisableTiming));
+  struct SideGuard {
+    cudaStream_t s;
+    cudaEvent_t a, b;
+    ~SideGuard() {
+      if (s) {
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+      }
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+  } side_guard{side, fork_ev, join_ev};
   std::vector<LevelRec<T>> recs(D + 1);
   size_t park_b_tot = 0, park_c_tot = 0;
-  int64_t apply_bytes = 0;
   double flops = 0;
 
   for (int l = 0; l <= D; ++l) {
@@ -405,9 +619,9 @@ static int factor_impl(const Plan& P, const bsr_matrix* A, double eps, int preci
           T* X = pm.alloc<T>((size_t)n[b] * n[s]);
           Ym[{s, b}] = Y;
           Xm[{b, s}] = X;
-          terms.push_back({Linv[q], Ap, n[s], n[s], n[s], 0, 0});
+          terms.push_back({Linv[q], Ap, n[s], n[s], n[s], 0, 0, 1});
           tasks.push_back({Y, n[s], n[s], n[b], (T)1, (T)0, (int)terms.size() - 1, (int)terms.size()});
-          terms.push_back({blk(b, s), Uinv[q], n[b], n[s], n[s], 0, 0});
+          terms.push_back({blk(b, s), Uinv[q], n[b], n[s], n[s], 0, 0, 2});
           tasks.push_back({X, n[b], n[b], n[s], (T)1, (T)0, (int)terms.size() - 1, (int)terms.size()});
           rec.nbr.push_back(b);
           rec.X.push_back(X);
@@ -418,6 +632,9 @@ static int factor_impl(const Plan& P, const bsr_matrix* A, double eps, int preci
       }
       if (tmp.err || pm.err) return SPAND_ERR_NOMEM;
       launch_row_perm(tmp, ps, pd, pp, pr_, pc_, st);
+      double gflops = 0;
+      for (size_t q = 0; q < tasks.size(); ++q) gflops += 1.0 * tasks[q].m * (double)tasks[q].n * terms[q].k;
+      ev_begin(ev_gm[l]);
       launch_gemm(tmp, tasks, terms, st);
       // Schur updates grouped by target block
       std::map<std::pair<int, int>, std::vector<int>> contrib;
@@ -435,10 +652,18 @@ static int factor_impl(const Plan& P, const bsr_matrix* A, double eps, int preci
           flops += 2.0 * n[a] * (double)n[b] * n[s];
         }
         tasks.push_back({blk(a, b), n[a], n[a], n[b], (T)-1, (T)1, t0, (int)terms.size()});
+        for (int q = t0; q < (int)terms.size(); ++q) gflops += 2.0 * n[a] * (double)n[b] * terms[q].k;
       }
       launch_gemm(tmp, tasks, terms, st);
+      ev_end(ev_gm[l]);
+      S.elim_gemm_flops += gflops;
+      S.elim_gemm_launches += 2;
       if (l == D)
         for (int s : I) S.top_size += n[s];
+      for (int s : I) {
+        const int q = P.system_of(l, s);
+        if (l == (P.sys_D.empty() ? D : P.sys_D[q])) F->sys_stats[q].top_size += n[s];
+      }
     }
     if (l == D) {
       tmp.free_all();
@@ -497,9 +722,9 @@ static int factor_impl(const Plan& P, const bsr_matrix* A, double eps, int preci
         pp.push_back(mats[fidx[a]].perm);
         pr_.push_back(n[a]);
         pc_.push_back(n[b]);
-        m1.push_back({SL[fidx[a]], Ap, n[a], n[a], n[a], 0, 0});
+        m1.push_back({SL[fidx[a]], Ap, n[a], n[a], n[a], 0, 0, 1});
         t1.push_back({Tm, n[a], n[a], n[b], (T)1, (T)0, (int)m1.size() - 1, (int)m1.size()});
-        m2.push_back({Tm, SU[fidx[b]], n[a], n[b], n[b], 0, 0});
+        m2.push_back({Tm, SU[fidx[b]], n[a], n[b], n[b], 0, 0, 2});
         t2.push_back({blk(a, b), n[a], n[a], n[b], (T)1, (T)0, (int)m2.size() - 1, (int)m2.size()});
         flops += 2.0 * n[a] * (double)n[b] * (n[a] + n[b]);
       }
@@ -547,23 +772,108 @@ static int factor_impl(const Plan& P, const bsr_matrix* A, double eps, int preci
     launch_copy(tmp, cps, st);
     std::vector<int> rank(qt.size());
     if (!qt.empty()) {
-      auto* dq = tmp.upload(qt);
-      const size_t sm = (size_t)nmax_qr * sizeof(T);
-      if (sm > kGemvSmemMax) return SPAND_ERR_UNSUPPORTED;
-      cudaFuncSetAttribute(k_qrcp_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemvSmemMax);
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3((unsigned)(qt.size() * QR_CS), 1, 1);
-      cfg.blockDim = dim3(QR_THREADS, 1, 1);
-      cfg.dynamicSmemBytes = sm;
-      cfg.stream = st;
-      cudaLaunchAttribute attr[1];
-      attr[0].id = cudaLaunchAttributeClusterDimension;
-      attr[0].val.clusterDim.x = QR_CS;
-      attr[0].val.clusterDim.y = 1;
-      attr[0].val.clusterDim.z = 1;
-      cfg.attrs = attr;
-      cfg.numAttrs = 1;
-      SPAND_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_qrcp_cluster<T>, (const QrTask<T>*)dq, (T)eps));
+      // reflector storage must be zero above the diagonal for the WY products
+      for (auto& q : qt) SPAND_CUDA_TRY(cudaMemsetAsync(q.V, 0, sizeof(T) * (size_t)q.n * std::min(q.n, q.c), st));
+      // 16-CTA clusters (non-portable size) where the device schedules them
+      // (per device: an on-chip probe of the two 16-CTA kernels)
+      static std::atomic<uint64_t> probed{0}, can16{0};
+      once_per_device(probed, [&] {
+        auto probe16 = [](auto kp, int nt) -> int {
+          if (cudaFuncSetAttribute(kp, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+          }
+          const long long lim = set_dyn_smem((const void*)kp, kQrSmemMax);
+          if (lim < 0) return 0;
+          cudaLaunchConfig_t probe = {};
+          cudaLaunchAttribute pa[1];
+          pa[0].id = cudaLaunchAttributeClusterDimension;
+          pa[0].val.clusterDim.x = 16;
+          pa[0].val.clusterDim.y = 1;
+          pa[0].val.clusterDim.z = 1;
+          probe.gridDim = dim3(16, 1, 1);
+          probe.blockDim = dim3(nt, 1, 1);
+          probe.dynamicSmemBytes = (size_t)lim;
+          probe.attrs = pa;
+          probe.numAttrs = 1;
+          int ncl = 0;
+          if (cudaOccupancyMaxActiveClusters(&ncl, kp, &probe) != cudaSuccess) ncl = 0;
+          cudaGetLastError();
+          return ncl;
+        };
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev >= 0 && dev < 64 && probe16(k_qrcp_cluster<T, false, 16, 1024>, 1024) > 0 &&
+            probe16(k_qrcp_cluster<T, true, 16, QR_THREADS>, QR_THREADS) > 0)
+          can16.fetch_or(uint64_t(1) << dev);
+      });
+      int cur_dev = 0;
+      cudaGetDevice(&cur_dev);
+      const int cl16 = (cur_dev >= 0 && cur_dev < 64 && ((can16.load() >> cur_dev) & 1)) ? 1 : 0;
+      // on-chip variants: chunk resident in shared memory with 8 or 16 CTAs;
+      // the rest streams W from L2 / HBM
+      std::vector<QrTask<T>> q_sm8, q_sm16, q_gl;
+      size_t sm8_max = 0, sm16_max = 0, gl_max = 0;
+      // what each on-chip kernel can be given next to its static shared memory
+      const long long lim8 = set_dyn_smem((const void*)k_qrcp_cluster<T, true, QR_CS, QR_THREADS>, kQrSmemMax);
+      const long long lim16 =
+          cl16 ? set_dyn_smem((const void*)k_qrcp_cluster<T, true, 16, QR_THREADS>, kQrSmemMax) : -1;
+      for (size_t k = 0; k < qt.size(); ++k) {
+        const size_t b8 = qrcp_smem_bytes<T>(qt[k].n, qt[k].c, QR_CS);
+        const size_t b16 = qrcp_smem_bytes<T>(qt[k].n, qt[k].c, 16);
+        if ((long long)b8 <= lim8) {
+          q_sm8.push_back(qt[k]);
+          sm8_max = std::max(sm8_max, b8);
+        } else if (cl16 && (long long)b16 <= lim16) {
+          q_sm16.push_back(qt[k]);
+          sm16_max = std::max(sm16_max, b16);
+        } else {
+          q_gl.push_back(qt[k]);
+          gl_max = std::max(gl_max, ((size_t)qt[k].n + 31) * sizeof(T));
+        }
+      }
+      // task arrays are uploaded on st before the fork, so the side stream
+      // never reads them ahead of their copies
+      QrTask<T>* d_gl = q_gl.empty() ? nullptr : tmp.upload(q_gl);
+      QrTask<T>* d_sm16 = q_sm16.empty() ? nullptr : tmp.upload(q_sm16);
+      QrTask<T>* d_sm8 = q_sm8.empty() ? nullptr : tmp.upload(q_sm8);
+      if (tmp.err) return SPAND_ERR_NOMEM;
+      auto launch_qr = [&](const QrTask<T>* dq, size_t count, cudaStream_t s2, int cs, int nt, size_t bytes,
+                           auto kern) -> int {
+        if (count == 0) return SPAND_OK;
+        if (cs > 8) SPAND_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        if (set_dyn_smem((const void*)kern, bytes) < (long long)bytes) return SPAND_ERR_UNSUPPORTED;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(count * cs), 1, 1);
+        cfg.blockDim = dim3(nt, 1, 1);
+        cfg.dynamicSmemBytes = bytes;
+        cfg.stream = s2;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        SPAND_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, dq, (T)eps));
+        return SPAND_OK;
+      };
+      ev_begin(ev_qr[l]);
+      // the streaming launch and the on-chip launches overlap on two streams
+      SPAND_CUDA_TRY(cudaEventRecord(fork_ev, st));
+      SPAND_CUDA_TRY(cudaStreamWaitEvent(side, fork_ev, 0));
+      if (cl16)
+        SPAND_TRY(launch_qr(d_gl, q_gl.size(), st, 16, 1024, gl_max, k_qrcp_cluster<T, false, 16, 1024>));
+      else
+        SPAND_TRY(launch_qr(d_gl, q_gl.size(), st, QR_CS, 1024, gl_max, k_qrcp_cluster<T, false, QR_CS, 1024>));
+      SPAND_TRY(launch_qr(d_sm16, q_sm16.size(), side, 16, QR_THREADS, sm16_max,
+                          k_qrcp_cluster<T, true, 16, QR_THREADS>));
+      SPAND_TRY(launch_qr(d_sm8, q_sm8.size(), side, QR_CS, QR_THREADS, sm8_max,
+                          k_qrcp_cluster<T, true, QR_CS, QR_THREADS>));
+      SPAND_CUDA_TRY(cudaEventRecord(join_ev, side));
+      SPAND_CUDA_TRY(cudaStreamWaitEvent(st, join_ev, 0));
+      ev_end(ev_qr[l]);
+      S.rrqr_launches += 1;
       SPAND_CUDA_TRY(cudaMemcpyAsync(rank.data(), d_rank, sizeof(int) * qt.size(), cudaMemcpyDeviceToHost, st));
     }
     int hflags[4];
@@ -571,6 +881,11 @@ static int factor_impl(const Plan& P, const bsr_matrix* A, double eps, int preci
     SPAND_CUDA_TRY(cudaStreamSynchronize(st));
     if (hflags[0] & 1) return SPAND_ERR_ZERO_PIVOT;   // the root cause when both are set
     if (hflags[0] & 2) return SPAND_ERR_NONFINITE;
+    S.t_rrqr_ms += ev_read(ev_qr[l]);
+    S.t_elim_gemm_ms += ev_read(ev_gm[l]);
+    for (size_t q = 0; q < qt.size(); ++q)
+      for (int k = 0; k < rank[q]; ++k)
+        S.rrqr_bytes += 2.0 * (double)(qt[q].n - k) * (double)(qt[q].c - k) * sizeof(T);
     std::vector<int> r(nc, 0);
     std::vector<char> spars(nc, 0);
     std::vector<T*> Qc(nc, nullptr);
@@ -585,11 +900,58 @@ static int factor_impl(const Plan& P, const bsr_matrix* A, double eps, int preci
       S.sum_n[l] += n[s];
       S.sum_r[l] += rank[q];
       S.max_r[l] = std::max<int64_t>(S.max_r[l], rank[q]);
+      spand_stats& Sq = F->sys_stats[P.system_of(l, s)];
+      Sq.n_sparsified[l] += 1;
+      Sq.sum_n[l] += n[s];
+      Sq.sum_r[l] += rank[q];
+      Sq.max_r[l] = std::max<int64_t>(Sq.max_r[l], rank[q]);
     }
     if (pm.err) return SPAND_ERR_NOMEM;
     if (!qt.empty()) {
-      auto* dq = tmp.upload(qt);
-      k_form_q_v<T><<<(unsigned)qt.size(), 512, 0, st>>>(dq);
+      // Q_c = [I_r; 0] - V M with M = T V_top^T (compact WY); G = V^T V first
+      std::vector<GemmTask<T>> gt, mt, qtk;
+      std::vector<GemmTerm<T>> gm, mm, qm;
+      std::vector<WyTask<T>> wy;
+      std::vector<MatRef<T>> tri;
+      std::vector<T*> Tinv;
+      std::vector<const T*> nod;
+      std::vector<EyeTask<T>> eye_q;
+      for (size_t q = 0; q < qt.size(); ++q) {
+        const int r = rank[q], nn = qt[q].n;
+        if (r <= 0) continue;
+        T* G = tmp.alloc<T>((size_t)r * r);
+        T* Tm = tmp.alloc<T>((size_t)r * r);
+        T* M = tmp.alloc<T>((size_t)r * r);
+        gm.push_back({qt[q].V, qt[q].V, nn, nn, nn, 1, 0});
+        gt.push_back({G, r, r, r, (T)1, (T)0, (int)gm.size() - 1, (int)gm.size()});
+        wy.push_back({G, qt[q].tau, r});
+        MatRef<T> mr;
+        mr.A = G;
+        mr.n = r;
+        mr.ipiv = nullptr;
+        mr.perm = nullptr;
+        tri.push_back(mr);
+        Tinv.push_back(Tm);
+        nod.push_back(nullptr);
+        mm.push_back({Tm, qt[q].V, r, nn, r, 0, 1});
+        mt.push_back({M, r, r, r, (T)1, (T)0, (int)mm.size() - 1, (int)mm.size()});
+        SPAND_CUDA_TRY(cudaMemsetAsync(qt[q].Q, 0, sizeof(T) * (size_t)nn * r, st));
+        eye_q.push_back({qt[q].Q, nn, r});
+        qm.push_back({qt[q].V, M, nn, r, r, 0, 0});
+        qtk.push_back({qt[q].Q, nn, nn, r, (T)-1, (T)1, (int)qm.size() - 1, (int)qm.size()});
+      }
+      if (tmp.err) return SPAND_ERR_NOMEM;
+      launch_gemm(tmp, gt, gm, st);
+      if (!wy.empty()) {
+        auto* dw = tmp.upload(wy);
+        k_wy_tinv<T><<<(unsigned)wy.size(), 256, 0, st>>>(dw);
+        // T = (T^-1)^-1 with the batched upper-triangular inverse
+        batched_upper_inverse(tmp, tri, Tinv, st);
+        auto* de = tmp.upload(eye_q);
+        k_eye<T><<<std::min<unsigned>((unsigned)eye_q.size(), 1024), 128, 0, st>>>(de, (int)eye_q.size());
+      }
+      launch_gemm(tmp, mt, mm, st);
+      launch_gemm(tmp, qtk, qm, st);
     }
     // records for the apply
     for (size_t q = 0; q < Fc.size(); ++q) {
@@ -672,6 +1034,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* A, double eps, int preci
     int hflags[4];
     SPAND_CUDA_TRY(cudaMemcpyAsync(hflags, d_flags, sizeof(hflags), cudaMemcpyDeviceToHost, st));
     SPAND_CUDA_TRY(cudaStreamSynchronize(st));
+    S.t_elim_gemm_ms += ev_read(ev_gm[D]);
     if (hflags[0] & 1) return SPAND_ERR_ZERO_PIVOT;   // the root cause when both are set
     if (hflags[0] & 2) return SPAND_ERR_NONFINITE;
   }
@@ -684,23 +1047,32 @@ static int factor_impl(const Plan& P, const bsr_matrix* A, double eps, int preci
   F->park_c = pm.alloc<T>(std::max<size_t>(park_c_tot, 1));
   if (pm.err) return SPAND_ERR_NOMEM;
   // permuted slot lists (P^T folded into the gather) for interiors and interfaces
-  for (int l = 0; l <= D; ++l) {
-    LevelRec<T>& R = recs[l];
-    for (auto& in : R.in) {
-      int* ps = pm.alloc<int>(in.n);
-      k_perm_slots<T><<<(in.n + 255) / 256, 256, 0, st>>>(R.d_slots[in.c], in.perm, ps, in.n);
-      R.d_pslots.push_back(ps);
+  std::vector<std::vector<int*>> fa_ps(D + 1);
+  {
+    std::vector<PermSlotTask> pt;
+    for (int l = 0; l <= D; ++l) {
+      LevelRec<T>& R = recs[l];
+      for (auto& in : R.in) {
+        int* ps = pm.alloc<int>(in.n);
+        pt.push_back({R.d_slots[in.c], in.perm, ps, in.n});
+        R.d_pslots.push_back(ps);
+      }
+      for (auto& f : R.fa) {
+        int* ps = pm.alloc<int>(f.n);
+        pt.push_back({R.d_slots[f.c], f.perm, ps, f.n});
+        fa_ps[l].push_back(ps);
+      }
+    }
+    if (pm.err) return SPAND_ERR_NOMEM;
+    if (!pt.empty()) {
+      DevMem tmpp;
+      tmpp.st = st;
+      auto* dpt = tmpp.upload(pt);
+      if (tmpp.err) return SPAND_ERR_NOMEM;
+      k_perm_slots<<<(unsigned)pt.size(), 256, 0, st>>>(dpt);
+      tmpp.free_all();
     }
   }
-  std::vector<int*> fa_pslots;
-  std::vector<std::vector<int*>> fa_ps(D + 1);
-  for (int l = 0; l <= D; ++l)
-    for (auto& f : recs[l].fa) {
-      int* ps = pm.alloc<int>(f.n);
-      k_perm_slots<T><<<(f.n + 255) / 256, 256, 0, st>>>(recs[l].d_slots[f.c], f.perm, ps, f.n);
-      fa_ps[l].push_back(ps);
-    }
-  if (pm.err) return SPAND_ERR_NOMEM;
   typedef typename ApplyProg<T>::Phase Phase;
   auto build = [&](std::vector<GvTask<T>>& tasks, std::vector<GvTerm<T>>& terms) -> Phase {
     Phase ph;
@@ -718,9 +1090,12 @@ static int factor_impl(const Plan& P, const bsr_matrix* A, double eps, int preci
   T* w = F->w;
   T* z = F->z;
   const size_t es = sizeof(T);
+  // sweeps of the clusters keep(l, c) selects (one system, or all of them)
+  auto build_prog = [&](Program<T>& pg, auto keep) {
+  int64_t& apply_bytes = pg.bytes;
   for (int tr = 0; tr < 2; ++tr) {
-    std::vector<Phase>& fwd = tr ? F->prog.tfwd : F->prog.fwd;
-    std::vector<Phase>& bwd = tr ? F->prog.tbwd : F->prog.bwd;
+    std::vector<Phase>& fwd = tr ? pg.prog.tfwd : pg.prog.fwd;
+    std::vector<Phase>& bwd = tr ? pg.prog.tbwd : pg.prog.bwd;
     for (int l = 0; l <= D; ++l) {
       LevelRec<T>& R = recs[l];
       std::vector<GvTask<T>> tk;
@@ -741,14 +1116,16 @@ static int factor_impl(const Plan& P, const bsr_matrix* A, double eps, int preci
       // neighbour -> interiors map for grouped coupling updates
       std::map<int, std::vector<std::pair<int, int>>> by_nb;   // b -> (interior index, nbr index)
       for (int q = 0; q < (int)R.in.size(); ++q)
-        for (int t = 0; t < (int)R.in[q].nbr.size(); ++t) by_nb[R.in[q].nbr[t]].push_back({q, t});
+        if (keep(l, R.in[q].c))
+          for (int t = 0; t < (int)R.in[q].nbr.size(); ++t) by_nb[R.in[q].nbr[t]].push_back({q, t});
       if (!tr) {
         // E1: z[s] = L^-1 P^T w[s]
         for (int q = 0; q < (int)R.in.size(); ++q) {
           auto& in = R.in[q];
+          if (!keep(l, in.c)) continue;
           task(z, R.d_slots[in.c], nullptr, nullptr, nullptr, (T)1, in.n);
           term(in.Linv, w, R.d_pslots[q], nullptr, in.n, in.n, 0, 1);
-          if (l == 0 || true) apply_bytes += (int64_t)in.n * (in.n + 1) / 2 * es;
+          apply_bytes += (int64_t)in.n * (in.n + 1) / 2 * es;
         }
         flush(fwd);
         // E2: w[b] -= sum_s X_bs z[s]
@@ -766,6 +1143,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* A, double eps, int preci
         // E3^T: z[s] = U^-T w[s];  w[b] -= Y_sb^T z[s]
         for (int q = 0; q < (int)R.in.size(); ++q) {
           auto& in = R.in[q];
+          if (!keep(l, in.c)) continue;
           task(z, R.d_slots[in.c], nullptr, nullptr, nullptr, (T)1, in.n);
           term(in.Uinv, w, R.d_slots[in.c], nullptr, in.n, in.n, 1, 2);
         }
@@ -784,6 +1162,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* A, double eps, int preci
         // S1: z[s] = SL P^T w[s]   (transpose: z[s] = SU^T w[s])
         for (size_t q = 0; q < R.fa.size(); ++q) {
           auto& f = R.fa[q];
+          if (!keep(l, f.c)) continue;
           task(z, R.d_slots[f.c], nullptr, nullptr, nullptr, (T)1, f.n);
           if (!tr) term(f.SL, w, fa_ps[l][q], nullptr, f.n, f.n, 0, 1);
           else term(f.SU, w, R.d_slots[f.c], nullptr, f.n, f.n, 1, 2);
@@ -792,6 +1171,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* A, double eps, int preci
         flush(fwd);
         // Q1: park z[s]; w[s][:r] = Q_c^T z[s]  (identity copy when unsparsified)
         for (auto& f : R.fa) {
+          if (!keep(l, f.c)) continue;
           if (f.sparsified) {
             task(F->park_b + f.park_b_off, nullptr, nullptr, nullptr, nullptr, (T)1, f.n);
             term(nullptr, z, R.d_slots[f.c], nullptr, f.n, f.n, 0, 0);
@@ -828,6 +1208,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* A, double eps, int preci
       if (l < D) {
         // Q2: z[s] = park_b + Q_c (w[s][:r] - park_c)
         for (auto& f : R.fa) {
+          if (!keep(l, f.c)) continue;
           task(z, R.d_slots[f.c], f.sparsified ? F->park_b + f.park_b_off : nullptr, nullptr, nullptr, (T)1, f.n);
           if (f.sparsified) {
             if (f.r > 0) {
@@ -842,6 +1223,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* A, double eps, int preci
         // S2: w[s] = SU z[s]   (transpose: w[P s] = SL^T z[s])
         for (size_t q = 0; q < R.fa.size(); ++q) {
           auto& f = R.fa[q];
+          if (!keep(l, f.c)) continue;
           if (!tr) {
             task(w, R.d_slots[f.c], nullptr, nullptr, nullptr, (T)1, f.n);
             term(f.SU, z, R.d_slots[f.c], nullptr, f.n, f.n, 0, 2);
@@ -857,7 +1239,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* A, double eps, int preci
       if (!tr) {
         // E3a: z[s] -= sum_b Y_sb w[b];  E3b: w[s] = U^-1 z[s]
         for (auto& in : R.in) {
-          if (in.nbr.empty()) continue;
+          if (in.nbr.empty() || !keep(l, in.c)) continue;
           task(z, R.d_slots[in.c], z, R.d_slots[in.c], nullptr, (T)-1, in.n);
           for (size_t t = 0; t < in.nbr.size(); ++t) {
             term(in.Y[t], w, R.d_slots[in.nbr[t]], nullptr, in.n, R.n[in.nbr[t]], 0, 0);
@@ -866,6 +1248,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* A, double eps, int preci
         }
         flush(bwd);
         for (auto& in : R.in) {
+          if (!keep(l, in.c)) continue;
           task(w, R.d_slots[in.c], nullptr, nullptr, nullptr, (T)1, in.n);
           term(in.Uinv, z, R.d_slots[in.c], nullptr, in.n, in.n, 0, 2);
           apply_bytes += (int64_t)in.n * (in.n + 1) / 2 * es;
@@ -874,7 +1257,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* A, double eps, int preci
       } else {
         // E2^T: z[s] -= sum_b X_bs^T w[b];  E1^T: w[P s] = L^-T z[s]
         for (auto& in : R.in) {
-          if (in.nbr.empty()) continue;
+          if (in.nbr.empty() || !keep(l, in.c)) continue;
           task(z, R.d_slots[in.c], z, R.d_slots[in.c], nullptr, (T)-1, in.n);
           for (size_t t = 0; t < in.nbr.size(); ++t)
             term(in.X[t], w, R.d_slots[in.nbr[t]], nullptr, R.n[in.nbr[t]], R.n[in.nbr[t]], 1, 0);
@@ -882,6 +1265,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* A, double eps, int preci
         flush(bwd);
         for (size_t q = 0; q < R.in.size(); ++q) {
           auto& in = R.in[q];
+          if (!keep(l, in.c)) continue;
           task(w, R.d_pslots[q], nullptr, nullptr, nullptr, (T)1, in.n);
           term(in.Linv, z, R.d_slots[in.c], nullptr, in.n, in.n, 1, 1);
         }
@@ -889,7 +1273,26 @@ static int factor_impl(const Plan& P, const bsr_matrix* A, double eps, int preci
       }
     }
   }
-  S.factor_bytes = apply_bytes;
+  };
+  F->progs.clear();
+  {
+    auto pg = std::make_unique<Program<T>>();
+    pg->off = 0;
+    pg->N = F->N;
+    build_prog(*pg, [](int, int) { return true; });
+    F->progs.push_back(std::move(pg));
+  }
+  if (nsys > 1)
+    for (int q = 0; q < nsys; ++q) {
+      auto pg = std::make_unique<Program<T>>();
+      pg->off = (int)sysDof0(q);
+      pg->N = sysK(q) * sysB(q);
+      build_prog(*pg, [&P, q](int l, int c) { return P.system_of(l, c) == q; });
+      F->sys_stats[q].factor_bytes = pg->bytes;
+      F->progs.push_back(std::move(pg));
+    }
+
+  S.factor_bytes = F->progs[0]->bytes;
   if (pm.err) return SPAND_ERR_NOMEM;
   SPAND_CUDA_TRY(cudaGetLastError());
   SPAND_CUDA_TRY(cudaStreamSynchronize(st));
@@ -902,12 +1305,16 @@ __global__ void k_convert(const Tin* a, Tout* b, int n) {
 }
 
 template <typename T>
+static void gemv_attr() {
+  static std::atomic<uint64_t> attr{0};
+  once_per_device(attr, [] {
+    set_dyn_smem((const void*)k_gemv<T>, kGemvSmemMax);
+  });
+}
+
+template <typename T>
 static int run_phases(const std::vector<typename ApplyProg<T>::Phase>& ph, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_gemv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemvSmemMax);
-    attr = true;
-  }
+  gemv_attr<T>();
   for (auto& p : ph) {
     const size_t sm = (size_t)std::max(p.kmax, 1) * sizeof(T);
     k_gemv<T><<<p.ntiles, 256, sm, st>>>(p.tasks, p.terms, p.tiles);
@@ -915,19 +1322,51 @@ static int run_phases(const std::vector<typename ApplyProg<T>::Phase>& ph, cudaS
   return SPAND_OK;
 }
 
+// The phase launches of one sweep pair never change for a factor, so they are
+// captured once per direction into a CUDA graph and replayed; the conversions
+// of the caller's r and z stay outside the graph.  When the caller's stream is
+// itself being captured, the phases are launched directly.
 template <typename T>
-static int apply_impl(FactorT<T>* F, const double* r, double* zout, int transpose, cudaStream_t st) {
-  const int N = F->N;
-  const unsigned g = (unsigned)std::min(4096, (N + 255) / 256);
-  k_convert<double, T><<<g, 256, 0, st>>>(r, F->w, N);
-  if (!transpose) {
-    run_phases<T>(F->prog.fwd, st);
-    run_phases<T>(F->prog.bwd, st);
+int apply_impl(FactorT<T>* F, Program<T>& pg, const double* r, double* zout, int transpose, cudaStream_t st) {
+  const int N = pg.N;
+  T* w = F->w + pg.off;
+  const unsigned g = (unsigned)std::max(1, std::min(4096, (N + 255) / 256));
+  k_convert<double, T><<<g, 256, 0, st>>>(r, w, N);
+  const int d = transpose ? 1 : 0;
+  const auto& fwd = transpose ? pg.prog.tfwd : pg.prog.fwd;
+  const auto& bwd = transpose ? pg.prog.tbwd : pg.prog.bwd;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  SPAND_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+  if (cs != cudaStreamCaptureStatusNone) {
+    run_phases<T>(fwd, st);
+    run_phases<T>(bwd, st);
   } else {
-    run_phases<T>(F->prog.tfwd, st);
-    run_phases<T>(F->prog.tbwd, st);
+    if (!pg.graph[d]) {
+      // a private stream for the capture keeps the caller's stream untouched
+      cudaStream_t cap;
+      SPAND_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+      gemv_attr<T>();            // function attributes are not captured: set them first
+      cudaGraph_t graph = nullptr;
+      bool ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        run_phases<T>(fwd, cap);
+        run_phases<T>(bwd, cap);
+        ok = cudaStreamEndCapture(cap, &graph) == cudaSuccess && graph;
+      }
+      if (ok) ok = cudaGraphInstantiate(&pg.graph[d], graph, 0) == cudaSuccess;
+      if (graph) cudaGraphDestroy(graph);
+      cudaStreamDestroy(cap);
+      cudaGetLastError();
+      if (!ok) pg.graph[d] = nullptr;
+    }
+    if (pg.graph[d]) {
+      SPAND_CUDA_TRY(cudaGraphLaunch(pg.graph[d], st));
+    } else {
+      run_phases<T>(fwd, st);
+      run_phases<T>(bwd, st);
+    }
   }
-  k_convert<T, double><<<g, 256, 0, st>>>(F->w, zout, N);
+  k_convert<T, double><<<g, 256, 0, st>>>(w, zout, N);
   SPAND_CUDA_TRY(cudaGetLastError());
   return SPAND_OK;
 }
@@ -935,24 +1374,48 @@ static int apply_impl(FactorT<T>* F, const double* r, double* zout, int transpos
 template <typename T>
 static int max_kmax(FactorT<T>* F) {
   int k = 1;
-  for (auto* v : {&F->prog.fwd, &F->prog.bwd, &F->prog.tfwd, &F->prog.tbwd})
-    for (auto& p : *v) k = std::max(k, p.kmax);
+  for (auto& pg : F->progs)
+    for (auto* v : {&pg->prog.fwd, &pg->prog.bwd, &pg->prog.tfwd, &pg->prog.tbwd})
+      for (auto& p : *v) k = std::max(k, p.kmax);
   return k;
+}
+
+// factorization of the union plan U (one system or several) into F
+static int factor_any(const Plan& U, const bsr_matrix* const* As, double eps, int precision, cudaStream_t stream,
+                      std::shared_ptr<FactorBase>& out) {
+  int st;
+  if (precision == SPAND_FP64) {
+    auto F = std::make_shared<FactorT<double>>();
+    out = F;
+    st = factor_impl<double>(U, As, eps, precision, F.get(), stream);
+    if (st == SPAND_OK && (size_t)max_kmax(F.get()) * sizeof(double) > kGemvSmemMax) st = SPAND_ERR_UNSUPPORTED;
+  } else {
+    auto F = std::make_shared<FactorT<float>>();
+    out = F;
+    st = factor_impl<float>(U, As, eps, precision, F.get(), stream);
+    if (st == SPAND_OK && (size_t)max_kmax(F.get()) * sizeof(float) > kGemvSmemMax) st = SPAND_ERR_UNSUPPORTED;
+  }
+  if (st != SPAND_OK) {
+    cudaStreamSynchronize(stream);
+    out->mem.free_all();
+    cudaStreamSynchronize(stream);
+    out.reset();
+  }
+  return st;
 }
 
 }  // namespace spand
 
 struct spand_factor_s {
-  std::unique_ptr<spand::FactorBase> impl;
+  std::shared_ptr<spand::FactorBase> impl;   // shared by the handles of one batched factorization
+  int prog = 0;                              // 0: every system; 1 + q: system q
 };
 
 namespace spand {
 int factor_apply(spand_factor_t F, const double* r, double* z, int transpose, cudaStream_t st) {
-  if (F->impl->precision == SPAND_FP64)
-    return apply_impl(static_cast<FactorT<double>*>(F->impl.get()), r, z, transpose, st);
-  return apply_impl(static_cast<FactorT<float>*>(F->impl.get()), r, z, transpose, st);
+  return F->impl->apply(F->prog, r, z, transpose, st);
 }
-int factor_size(spand_factor_t F) { return F->impl->N; }
+int factor_size(spand_factor_t F) { return F->impl->prog_size(F->prog); }
 }  // namespace spand
 
 extern "C" {
@@ -965,26 +1428,8 @@ int spand_factor(spand_plan_t plan, const bsr_matrix* A, double eps, int precisi
   if (precision != SPAND_FP64 && precision != SPAND_MIXED) return SPAND_ERR_ARG;
   spand_factor_s* f = new (std::nothrow) spand_factor_s();
   if (!f) return SPAND_ERR_NOMEM;
-  int st;
-  if (precision == SPAND_FP64) {
-    auto* F = new (std::nothrow) spand::FactorT<double>();
-    f->impl.reset(F);
-    st = F ? spand::factor_impl<double>(plan->P, A, eps, precision, F, stream) : SPAND_ERR_NOMEM;
-    if (st == SPAND_OK && (size_t)spand::max_kmax(F) * sizeof(double) > spand::kGemvSmemMax)
-      st = SPAND_ERR_UNSUPPORTED;
-  } else {
-    auto* F = new (std::nothrow) spand::FactorT<float>();
-    f->impl.reset(F);
-    st = F ? spand::factor_impl<float>(plan->P, A, eps, precision, F, stream) : SPAND_ERR_NOMEM;
-    if (st == SPAND_OK && (size_t)spand::max_kmax(F) * sizeof(float) > spand::kGemvSmemMax)
-      st = SPAND_ERR_UNSUPPORTED;
-  }
+  const int st = spand::factor_any(plan->P, &A, eps, precision, stream, f->impl);
   if (st != SPAND_OK) {
-    if (f->impl) {
-      cudaStreamSynchronize(stream);
-      f->impl->mem.free_all();
-      cudaStreamSynchronize(stream);
-    }
     delete f;
     return st;
   }
@@ -992,9 +1437,48 @@ int spand_factor(spand_plan_t plan, const bsr_matrix* A, double eps, int precisi
   return SPAND_OK;
 }
 
+int spand_factor_batched(int nsys, const spand_plan_t* plans, const bsr_matrix* A, double eps, int precision,
+                         spand_factor_t* out, cudaStream_t stream) {
+  if (nsys <= 0 || !plans || !A || !out || !(eps >= 0.0)) return SPAND_ERR_ARG;
+  if (precision != SPAND_FP64 && precision != SPAND_MIXED) return SPAND_ERR_ARG;
+  for (int q = 0; q < nsys; ++q) out[q] = nullptr;
+  std::vector<const spand::Plan*> ps(nsys);
+  std::vector<const bsr_matrix*> as(nsys);
+  for (int q = 0; q < nsys; ++q) {
+    if (!plans[q] || !A[q].row_ptr || !A[q].col || !A[q].val) return SPAND_ERR_ARG;
+    if (A[q].K != plans[q]->P.K || A[q].B != plans[q]->P.B) return SPAND_ERR_ARG;
+    ps[q] = &plans[q]->P;
+    as[q] = &A[q];
+  }
+  spand::Plan U;
+  int st = spand::build_union_plan(ps, U);
+  if (st != SPAND_OK) return st;
+  std::shared_ptr<spand::FactorBase> impl;
+  st = spand::factor_any(U, as.data(), eps, precision, stream, impl);
+  if (st != SPAND_OK) return st;
+  for (int q = 0; q < nsys; ++q) {
+    spand_factor_s* f = new (std::nothrow) spand_factor_s();
+    if (!f) {
+      for (int k = 0; k < q; ++k) {
+        delete out[k];
+        out[k] = nullptr;
+      }
+      cudaStreamSynchronize(stream);
+      impl->mem.free_all();
+      cudaStreamSynchronize(stream);
+      return SPAND_ERR_NOMEM;
+    }
+    f->impl = impl;
+    f->prog = nsys > 1 ? 1 + q : 0;
+    out[q] = f;
+  }
+  return SPAND_OK;
+}
+
 int spand_factor_destroy(spand_factor_t F) {
   if (!F) return SPAND_OK;
-  if (F->impl) {
+  if (F->impl && F->impl.use_count() == 1) {
+    // the last handle of the factorization releases its device memory
     cudaDeviceSynchronize();
     F->impl->mem.free_all();
     cudaDeviceSynchronize();
@@ -1005,7 +1489,21 @@ int spand_factor_destroy(spand_factor_t F) {
 
 int spand_factor_stats(spand_factor_t F, spand_stats* st) {
   if (!F || !st) return SPAND_ERR_ARG;
-  *st = F->impl->stats;
+  const spand::FactorBase& B = *F->impl;
+  if (F->prog == 0) {
+    *st = B.stats;
+  } else {
+    // the system's own ranks and bytes; phase times and flops are those of the
+    // whole batched factorization
+    *st = B.sys_stats[F->prog - 1];
+    st->factor_flops = B.stats.factor_flops;
+    st->t_rrqr_ms = B.stats.t_rrqr_ms;
+    st->rrqr_bytes = B.stats.rrqr_bytes;
+    st->rrqr_launches = B.stats.rrqr_launches;
+    st->t_elim_gemm_ms = B.stats.t_elim_gemm_ms;
+    st->elim_gemm_flops = B.stats.elim_gemm_flops;
+    st->elim_gemm_launches = B.stats.elim_gemm_launches;
+  }
   return SPAND_OK;
 }
 

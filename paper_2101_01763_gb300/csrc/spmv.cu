@@ -184,11 +184,8 @@ int block_update(int64_t N, int s, int ny, const double* Y, int64_t ldy, const d
                  cudaStream_t st) {
   if (s > 16) return SPAND_ERR_ARG;
   const size_t sm = (size_t)(ny + nz) * s * sizeof(double);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_block_update, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  once_per_device(attr, [] { set_dyn_smem((const void*)k_block_update, 200 * 1024); });
   const unsigned g = (unsigned)std::min<int64_t>(152 * 8, (N + 255) / 256);
   k_block_update<<<g, 256, sm, st>>>(N, s, ny, Y, ldy, Sinv, nz, Z, ldz, C, ldc, X, ldx, accumulate);
   return cudaGetLastError() == cudaSuccess ? SPAND_OK : SPAND_ERR_CUDA;
@@ -218,7 +215,33 @@ int axpy_dev(int64_t N, const double* coef, double sign, const double* x, double
   return cudaGetLastError() == cudaSuccess ? SPAND_OK : SPAND_ERR_CUDA;
 }
 
+// out[k] = alpha * u_row(k) v_col(k)^T for every stored block k (column-major)
+__global__ void __launch_bounds__(256) k_pattern_outer(int K, int B, const int* __restrict__ row_ptr,
+                                                       const int* __restrict__ col, const double* __restrict__ u,
+                                                       const double* __restrict__ v, double alpha,
+                                                       double* __restrict__ out) {
+  const int e = blockIdx.x;
+  if (e >= K) return;
+  const size_t bb = (size_t)B * B;
+  for (int k = row_ptr[e]; k < row_ptr[e + 1]; ++k) {
+    const double* ue = u + (size_t)e * B;
+    const double* vc = v + (size_t)col[k] * B;
+    double* o = out + (size_t)k * bb;
+    for (int idx = threadIdx.x; idx < B * B; idx += blockDim.x) {
+      const int r = idx % B, c = idx / B;
+      o[idx] = alpha * ue[r] * vc[c];
+    }
+  }
+}
+
 }  // namespace spand
+
+extern "C" int bsr_pattern_outer(const bsr_matrix* A, const double* u, const double* v, double alpha, double* out,
+                                 cudaStream_t stream) {
+  if (!A || !u || !v || !out || !A->row_ptr || !A->col || A->K <= 0 || A->B <= 0) return SPAND_ERR_ARG;
+  spand::k_pattern_outer<<<A->K, 256, 0, stream>>>(A->K, A->B, A->row_ptr, A->col, u, v, alpha, out);
+  return cudaGetLastError() == cudaSuccess ? SPAND_OK : SPAND_ERR_CUDA;
+}
 
 extern "C" int bsr_spmv(const bsr_matrix* A, const double* x, double* y, int transpose, cudaStream_t stream) {
   if (!A || !x || !y || x == y || !A->row_ptr || !A->col || !A->val || A->K <= 0 || A->B <= 0) return SPAND_ERR_ARG;
