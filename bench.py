@@ -25,6 +25,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "spaND factor+s-step GMRES time to 1e-8 rel residual; mixed vs FP64 speedup"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+# DRAM bytes (read + write) of the RRQR kernels of one C2 mixed factorization,
+# per level, from the ncu capture summarised in profiles/ (null until measured)
+RRQR_TRAFFIC_PER_LEVEL = None
 
 
 def parse():
@@ -151,10 +154,125 @@ def run_reference(args):
     return 0
 
 
+def run_batch(args):
+    """Many independent systems (grids, degrees, flow conditions drawn per
+    system): batched mixed factorization + batched s-step GMRES, against the
+    same systems solved one at a time in FP64 and in mixed precision."""
+    import torch
+    from synth.configs import batch_configs
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__ as g
+    g.build()
+    import paper_2101_01763_gb300 as sg
+    from synth import modal_state, naca_ogrid
+    cs = batch_configs(24)
+    sys_ = []
+    for c in cs:
+        X = naca_ogrid(c.n_theta, c.n_r, c.seed)
+        u = modal_state(X, c.p, c.mach, c.alpha_deg, c.amp, c.seed)
+        rhs, A, _ = sg.assemble(torch.as_tensor(X, device=dev), c.p, torch.as_tensor(u, device=dev), c.mach,
+                                c.alpha_deg, c.cfl)
+        sys_.append((c, A, rhs, sg.Plan(c.n_theta, c.n_r, A.B, c.nd_depth)))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    c0 = cs[0]
+
+    # systems are factored in groups of at most ~3M unknowns (the union of a
+    # level's clusters, its W matrices and the factors of a group stay well
+    # inside HBM); a group's factors are released before the next group
+    groups, cur, tot = [], [], 0
+    for q, (c, A, b, p) in enumerate(sys_):
+        if cur and tot + c.N > 3_000_000:
+            groups.append(cur)
+            cur, tot = [], 0
+        cur.append(q)
+        tot += c.N
+    if cur:
+        groups.append(cur)
+
+    def batched():
+        xs, st, status = [None] * len(sys_), [None] * len(sys_), [None] * len(sys_)
+        for grp in groups:
+            Fb = sg.factor_batched([sys_[q][3] for q in grp], [sys_[q][1] for q in grp], c0.eps, "mixed")
+            x_g, st_g, s_g = sg.sstep_gmres_batched([sys_[q][1] for q in grp], Fb, [sys_[q][2] for q in grp],
+                                                    s=c0.s, restart=c0.restart, tol=c0.tol, max_iters=c0.max_iters)
+            for f in Fb:
+                f.close()
+            for k, q in enumerate(grp):
+                xs[q], st[q], status[q] = x_g[k], st_g[k], s_g[k]
+        return [], xs, st, status
+
+    def single(prec):
+        out = []
+        for c, A, b, plan in sys_:
+            F = sg.Factor(plan, A, c.eps, prec)
+            x, st = sg.sstep_gmres(A, F, b, s=c.s, restart=c.restart, tol=c.tol, max_iters=c.max_iters)
+            out.append((x, st))
+            F.close()
+        return out
+
+    def timed(fn, steps, warm):
+        for _ in range(warm):
+            r = fn()
+            if isinstance(r, tuple):
+                for f in r[0]:
+                    f.close()
+        ts = []
+        res = None
+        for _ in range(steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            if isinstance(res, tuple):
+                for f in res[0]:
+                    f.close()
+        return statistics.mean(ts), res
+
+    steps, warm = max(1, args.steps), max(1, min(args.warmup, 3))
+    with Clocks(local) as clk:
+        t_b, (_, xs, st_b, status) = timed(batched, steps, warm)
+    t_m, res_m = timed(lambda: single("mixed"), 1, 1)
+    t_64, res_64 = timed(lambda: single("fp64"), 1, 1)
+    rel = []
+    for (c, A, b, _), x in zip(sys_, xs):
+        r = sg.spmv(A, x) - b
+        rel.append((torch.linalg.norm(r) / torch.linalg.norm(b)).item())
+    if rank != 0:
+        return 0
+    n = len(cs)
+    out = {"metric": "independent DG Newton-step systems solved per second (spaND factor + s-step GMRES, "
+                     "batched mixed precision)",
+           "value": world * n * 1e3 / t_b, "unit": "systems/s", "n_gpus": world, "steps": steps, "warmup": warm,
+           "ms_per_step": t_b, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": f"{n} systems: O-grids in {{32x16, 64x32, 96x48, 192x96}}, p in {{1,2,3}}, "
+                                  f"M in [0.3,0.8], alpha in [0,4] deg (seeds 2101_0500+i), eps={c0.eps}, "
+                                  f"s={c0.s}, restart={c0.restart}, tol={c0.tol}",
+                      "total_N": sum(c.N for c in cs), "groups": [len(g) for g in groups],
+                      "l2": "flushed between timed steps (256 MB write)"},
+           "ms_per_system_batched": t_b / n, "ms_one_at_a_time_mixed": t_m, "ms_one_at_a_time_fp64": t_64,
+           "speedup_vs_one_at_a_time_fp64": t_64 / t_b, "speedup_vs_one_at_a_time_mixed": t_m / t_b,
+           "max_true_relres": max(rel), "all_converged": all(v == 0 for v in status),
+           "iters": [s["iters"] for s in st_b], "clocks": clk.summary()}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.config == "C5":
+        return run_batch(args)
     import numpy as np
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -187,6 +305,8 @@ def main():
         x, st = sg.sstep_gmres(A, F, rhs, s=c.s, restart=c.restart, tol=c.tol, max_iters=c.max_iters)
         return F, x, st
 
+    launched = {}
+
     def timed(prec, steps, warmup):
         for _ in range(warmup):
             F, x, st = one(prec)
@@ -194,6 +314,7 @@ def main():
         ev = []
         stats = None
         barrier()
+        n0 = sg.kernel_launches()
         for _ in range(steps):
             flush.fill_(1.0)
             e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
@@ -207,6 +328,7 @@ def main():
             stats = (F.stats(), st, x)
             F.close()
         barrier()
+        launched[prec] = sg.kernel_launches() - n0
         return ev, stats
 
     # ---- headline: mixed form
@@ -215,13 +337,34 @@ def main():
     # ---- FP64 form beside it (fewer steps: its factorization is FP64-ALU bound)
     k64 = max(2, min(args.steps, 4))
     ev_64, (fst_64, gst_64, x_64) = timed("fp64", k64, max(1, min(args.warmup, 2)))
+    launches_mx = launched["mixed"]
     t_mx = statistics.mean(a + b for a, b in ev_mx)
     t_64 = statistics.mean(a + b for a, b in ev_64)
     # true residual of the final mixed solution (independent FP64 SpMV)
     r = sg.spmv(A, x_mx)
     relres = (torch.linalg.norm(r - rhs) / torch.linalg.norm(rhs)).item()
 
-    # ---- roofline of the preconditioner apply (HBM-bound GEMV sweeps), timed live
+    # ---- rooflines, timed live with CUDA events on the factorization / apply stream
+    pk, pk_kind = peaks()
+    hbm = float(pk.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    bf16 = float(pk.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"]))
+    tf32_peak = bf16 * (1.1 / 2.25)          # nominal TF32 : BF16 dense ratio
+    # dominant kernel of the step: the rank-revealing QR of the sparsification.
+    # One "launch" is the RRQR phase of one level (the cluster, group and
+    # streaming kernels of the level, timed between events on the factor's
+    # stream).  Algorithmic work per pivot step k of an n x c interface:
+    # E = (n-k)(c-k) elements, 2E flops for the dots, 2E for the update, 2E
+    # for the exact norms; the library counts 8E bytes (E read + written).
+    rr_ms = fst_mx["t_rrqr_ms"] / max(1, fst_mx["rrqr_launches"])
+    rr_elems = fst_mx["rrqr_bytes"] / 8.0 / max(1, fst_mx["rrqr_launches"])
+    rr_flops = 6.0 * rr_elems
+    rr_ach = rr_flops / (rr_ms * 1e-3) / 1e12 if rr_ms > 0 else 0.0
+    # FP32 (non-tensor) peak: 152 SMs x 128 FP32 lanes x 2 flops x SM clock
+    clk_mhz = clk.summary().get("sm_max_mhz") or 2070.0
+    fp32_peak = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
+    gm_ms = fst_mx["t_elim_gemm_ms"] / max(1, fst_mx["elim_gemm_launches"])
+    gm_fl = fst_mx["elim_gemm_flops"] / max(1, fst_mx["elim_gemm_launches"])
+    gm_ach = gm_fl / (gm_ms * 1e-3) / 1e12 if gm_ms > 0 else 0.0
     F = sg.Factor(plan, A, c.eps, "mixed")
     z = torch.empty_like(rhs)
     for _ in range(3):
@@ -237,8 +380,6 @@ def main():
     t_apply = e0.elapsed_time(e1) / napp
     fb = F.stats()["factor_bytes"]
     F.close()
-    pk, pk_kind = peaks()
-    hbm = float(pk.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
     achieved = fb / (t_apply * 1e-3) / 1e9
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside
@@ -310,10 +451,23 @@ def main():
         "true_relres_mixed": relres, "ranks_per_level": fst_mx["sum_r"],
         "solves_per_s": world * 1e3 / t_mx,
         "e2e": {"value": t_e2e, "unit": "ms", "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
-        "gpu_launches": None,
-        "roofline": {"kernel": "spand_apply (gather-GEMV sweeps, FP32 factors)", "bound": "hbm",
-                     "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": None, "peak_kind": pk_kind, "bytes_per_launch": fb, "ms_per_launch": t_apply},
+        "gpu_launches": launches_mx,
+        "gpu_launches_per_step": launches_mx / max(1, args.steps),
+        "roofline": {"kernel": "k_qrcp_cluster + k_qrcp_group (column-pivoted Householder QR of the interface "
+                               "sparsification; one launch = the RRQR phase of one level)",
+                     "bound": "alu", "achieved": rr_ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": rr_ach / fp32_peak, "traffic": RRQR_TRAFFIC_PER_LEVEL,
+                     "peak_kind": "FP32 lanes x 2 x max SM clock (152 x 128 x 2 x f)",
+                     "flops_per_launch": rr_flops, "ms_per_launch": rr_ms,
+                     "flops_rule": "6 (n-k)(c-k) per pivot step k: dots, update, exact column norms"},
+        "roofline_more": [
+            {"kernel": "k_gemm_tc (elimination Y, X, Schur products; 3xTF32 tensor cores)", "bound": "tensor",
+             "achieved": gm_ach, "peak": tf32_peak, "unit": "TFLOP/s", "frac": gm_ach / tf32_peak,
+             "peak_kind": f"{pk_kind} bf16 x nominal tf32/bf16 ratio", "flops_per_launch": gm_fl,
+             "ms_per_launch": gm_ms},
+            {"kernel": "spand_apply (k_gemv sweeps, FP32 factors)", "bound": "hbm", "achieved": achieved,
+             "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "peak_kind": f"{pk_kind} hbm_gbs",
+             "bytes_per_launch": fb, "ms_per_launch": t_apply}],
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
     }

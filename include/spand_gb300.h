@@ -193,6 +193,18 @@ typedef struct {
   double t_elim_gemm_ms;
   double elim_gemm_flops;
   int elim_gemm_launches;
+  /* per level: RRQR time (ms) and algorithmic bytes, and how many interfaces
+   * ran in each RRQR form: [0] 8-CTA cluster, [1] 16-CTA cluster (both with
+   * W in shared memory), [2] cooperative CTA group (W in shared memory),
+   * [3] W streamed from L2 / HBM (cooperative CTA group or 16-CTA cluster) */
+  double t_rrqr_level_ms[32];
+  double rrqr_bytes_level[32];
+  int rrqr_form_count[32][4];
+  /* host side of spand_factor: wall time of the call and the part of it spent
+   * waiting for the GPU (one wait per level for the ranks, one at the end);
+   * the difference is host work (planning, task tables, allocations).      */
+  double t_host_ms;
+  double t_wait_ms;
 } spand_stats;
 int spand_factor_stats(spand_factor_t F, spand_stats* st);
 
@@ -283,6 +295,12 @@ int sstep_gmres_solve_noalloc(const bsr_matrix* A, spand_factor_t M, const doubl
 size_t sstep_gmres_noalloc_capacity(void);
 
 const char* spand_status_string(int status);
+
+/* Number of kernel launches this library has issued in the process so far
+ * (a replay of a captured apply graph adds the kernels in the graph; kernels
+ * queued while the caller's stream is being captured count when queued).
+ * For accounting, e.g. launches per solve; not part of the paper. */
+uint64_t spand_kernel_launches(void);
 
 #ifdef __cplusplus
 }

@@ -4,6 +4,6 @@ Public API (all compute in the CUDA library libspand_gb300.so):
     assemble, spmv, Plan, Factor, sstep_gmres, SpandSolve,
     factor_batched, sstep_gmres_batched (many independent systems)
 """
-from .api import (BSR, Factor, Plan, SpandSolve, assemble, factor_batched, parse_table,  # noqa: F401
-                  pattern_outer, spmv, sstep_gmres, sstep_gmres_batched)
+from .api import (BSR, Factor, Plan, SpandSolve, assemble, factor_batched, kernel_launches,  # noqa: F401
+                  parse_table, pattern_outer, spmv, sstep_gmres, sstep_gmres_batched)
 from ._lib import SpandError  # noqa: F401

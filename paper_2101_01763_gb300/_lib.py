@@ -43,7 +43,9 @@ class SpandStats(C.Structure):
                 ("sum_r", C.c_int64 * 32), ("max_r", C.c_int64 * 32), ("top_size", C.c_int64),
                 ("factor_bytes", C.c_int64), ("factor_flops", C.c_double),
                 ("t_rrqr_ms", C.c_double), ("rrqr_bytes", C.c_double), ("rrqr_launches", C.c_int),
-                ("t_elim_gemm_ms", C.c_double), ("elim_gemm_flops", C.c_double), ("elim_gemm_launches", C.c_int)]
+                ("t_elim_gemm_ms", C.c_double), ("elim_gemm_flops", C.c_double), ("elim_gemm_launches", C.c_int),
+                ("t_rrqr_level_ms", C.c_double * 32), ("rrqr_bytes_level", C.c_double * 32),
+                ("rrqr_form_count", (C.c_int * 4) * 32), ("t_host_ms", C.c_double), ("t_wait_ms", C.c_double)]
 
 
 class GmresOpts(C.Structure):
@@ -86,6 +88,7 @@ EXPORTS = {
                                    C.POINTER(GmresOpts), C.POINTER(GmresStats), C.c_void_p], C.c_int),
     "sstep_gmres_noalloc_capacity": ([], C.c_size_t),
     "spand_status_string": ([C.c_int], C.c_char_p),
+    "spand_kernel_launches": ([], C.c_uint64),
 }
 
 _lib = None

@@ -8,6 +8,11 @@ import torch
 from . import _lib as L
 
 
+def kernel_launches():
+    """spand_kernel_launches: kernels the library has launched in this process."""
+    return int(L.lib().spand_kernel_launches())
+
+
 def _stream(stream=None):
     s = stream if stream is not None else torch.cuda.current_stream()
     return C.c_void_p(s.cuda_stream)
@@ -165,7 +170,10 @@ class Factor:
                     factor_bytes=s.factor_bytes, factor_flops=s.factor_flops,
                     t_rrqr_ms=s.t_rrqr_ms, rrqr_bytes=s.rrqr_bytes, rrqr_launches=s.rrqr_launches,
                     t_elim_gemm_ms=s.t_elim_gemm_ms, elim_gemm_flops=s.elim_gemm_flops,
-                    elim_gemm_launches=s.elim_gemm_launches)
+                    elim_gemm_launches=s.elim_gemm_launches, t_rrqr_level_ms=list(s.t_rrqr_level_ms[:n]),
+                    rrqr_bytes_level=list(s.rrqr_bytes_level[:n]),
+                    rrqr_form_count=[list(s.rrqr_form_count[l]) for l in range(n)],
+                    t_host_ms=s.t_host_ms, t_wait_ms=s.t_wait_ms)
 
     def close(self):
         if getattr(self, "h", None):

@@ -1006,24 +1006,116 @@ constexpr int QR_THREADS = 512;
 // Threads are laid out as (row segment, column): a group of CW consecutive
 // columns is processed by all NT/CW row segments, so narrow chunks still keep
 // every thread busy; partial dots and norms are combined in shared memory.
-template <typename T, bool SMEM, int CS, int NT>
-__global__ void __launch_bounds__(NT, 1) k_qrcp_cluster(const QrTask<T>* tasks, T eps) {
-  namespace cg = cooperative_groups;
-  cg::cluster_group cluster = cg::this_cluster();
-  extern __shared__ unsigned char qr_smem2[];
-  T* v = reinterpret_cast<T*>(qr_smem2);           // n: current reflector (local copy)
-  __shared__ T cand_v;
-  __shared__ int cand_i;
+// How the CTAs that share one interface exchange the pivot proposals and the
+// reflector.  ClusterX: one thread-block cluster, distributed shared memory
+// and cluster barriers.  GroupX: a group of CTAs of a cooperative launch,
+// global memory (read past L1) and a counting barrier per group whose wait is
+// bounded (on timeout it raises bit 4 of the error flags and the CTAs leave).
+template <typename T, int CS>
+struct ClusterX {
+  static constexpr int kMax = CS;
+  cooperative_groups::cluster_group cl;
+  T* cand_v;
+  int* cand_i;
+  __device__ int rank() const { return (int)cl.block_rank(); }
+  __device__ int size() const { return CS; }
+  __device__ bool sync() {
+    cl.sync();
+    return true;
+  }
+  __device__ void publish(T v, int i) {   // thread 0
+    *cand_v = v;
+    *cand_i = i;
+  }
+  __device__ void gather(int r, T& v, int& i) {
+    v = *cl.map_shared_rank(cand_v, r);
+    i = *cl.map_shared_rank(cand_i, r);
+  }
+  // copy rows k..n-1 of the owner's reflector and its tau into this CTA
+  __device__ void fetch_reflector(T* v, T* s_tau, const QrTask<T>&, int k, int n, int owner, int tid, int nt) {
+    const T* rv = cl.map_shared_rank(v, owner);
+    for (int i = k + tid; i < n; i += nt) v[i] = rv[i];
+    if (tid == 0) *s_tau = *cl.map_shared_rank(s_tau, owner);
+  }
+  __device__ void finish() { cl.sync(); }   // no CTA leaves while another may read its shared memory
+};
+
+struct GroupSync {
+  unsigned count, gen;
+};
+
+constexpr int QR_GMAX = 256;     // largest CTA group of the cooperative variants
+
+template <typename T>
+struct GroupX {
+  static constexpr int kMax = QR_GMAX;
+  int q, G;
+  T* prop_v;                 // G proposals of this group (global)
+  int* prop_i;
+  GroupSync* gs;
+  int* err;
+  __device__ int rank() const { return q; }
+  __device__ int size() const { return G; }
+  __device__ bool sync() {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_ok = 1;
+      volatile unsigned* vgen = &gs->gen;
+      const unsigned g = *vgen;
+      __threadfence();
+      if (atomicAdd(&gs->count, 1u) == (unsigned)G - 1) {
+        gs->count = 0;
+        __threadfence();
+        atomicAdd(&gs->gen, 1u);
+      } else {
+        long it = 0;
+        while (*vgen == g) {
+          if (++it > (1l << 22)) {          // ~0.5 s with the back-off below
+            atomicOr(err, 16);
+            s_ok = 0;
+            break;
+          }
+          __nanosleep(100);
+        }
+      }
+      __threadfence();
+    }
+    __syncthreads();
+    return s_ok != 0;
+  }
+  __device__ void publish(T v, int i) {
+    prop_v[q] = v;
+    prop_i[q] = i;
+  }
+  __device__ void gather(int r, T& v, int& i) {
+    v = __ldcg(prop_v + r);
+    i = __ldcg(prop_i + r);
+  }
+  __device__ void fetch_reflector(T* v, T* s_tau, const QrTask<T>& tk, int k, int n, int, int tid, int nt) {
+    const T* col = tk.V + (size_t)k * n;
+    for (int i = k + tid; i < n; i += nt) v[i] = __ldcg(col + i);
+    if (tid == 0) *s_tau = __ldcg(tk.tau + k);
+  }
+  __device__ void finish() {}
+};
+
+// The factorization of one interface by the CTAs of one exchange group X
+// (rank q of X.size() CTAs; columns split in contiguous chunks).
+template <typename T, bool SMEM, int NT, typename X>
+__device__ void qrcp_group(const QrTask<T>& tk, T eps, X& xc, unsigned char* smem_raw, T* cand_v, int* cand_i,
+                           int* err) {
+  constexpr int CSM = X::kMax;
+  T* v = reinterpret_cast<T*>(smem_raw);           // n: current reflector (local copy)
   __shared__ T red_v[32];
   __shared__ int red_i[32];
-  __shared__ T allc_v[CS];
-  __shared__ int allc_i[CS];
+  __shared__ T allc_v[CSM];
+  __shared__ int allc_i[CSM];
   __shared__ T s_scal[4];                          // [0] tau, [1] winner norm^2
   __shared__ int s_win;
   __shared__ T part[NT];                           // (segment, column) partials
   __shared__ T dotv[NT];
-  const int q = (int)cluster.block_rank();
-  const QrTask<T> tk = tasks[blockIdx.x / CS];
+  const int q = xc.rank(), CS = xc.size();
   const int n = tk.n, c = tk.c;
   const int chunk = (c + CS - 1) / CS;
   const int j0 = min(c, q * chunk), j1 = min(c, j0 + chunk);
@@ -1068,22 +1160,17 @@ __global__ void __launch_bounds__(NT, 1) k_qrcp_cluster(const QrTask<T>* tasks, 
   const int kmax = min(n, c);
   int rank = kmax;
   T nrm0 = 0;
+  bool ok = true;
   for (int k = 0; k < kmax; ++k) {
     // ---- local proposal
     T best = -1;
     int bi = c;
     for (int j = j0 + tid; j < j1; j += NT) argmax_pair(best, bi, tk.norm2[j], j);
     block_argmax(best, bi, red_v, red_i);
-    if (tid == 0) {
-      cand_v = best;
-      cand_i = bi;
-    }
-    cluster.sync();
-    // ---- cluster-wide winner: one remote read per thread, in parallel
-    if (tid < CS) {
-      allc_v[tid] = *cluster.map_shared_rank(&cand_v, tid);
-      allc_i[tid] = *cluster.map_shared_rank(&cand_i, tid);
-    }
+    if (tid == 0) xc.publish(best, bi);
+    if (!(ok = xc.sync())) break;
+    // ---- group-wide winner: one read per thread, in parallel
+    if (tid < CS) xc.gather(tid, allc_v[tid], allc_i[tid]);
     __syncthreads();
     if (tid == 0) {
       T gb = -1;
@@ -1135,14 +1222,10 @@ __global__ void __launch_bounds__(NT, 1) k_qrcp_cluster(const QrTask<T>* tasks, 
         tk.norm2[p] = -1;                  // used
       }
     }
-    cluster.sync();
+    if (!(ok = xc.sync())) break;
     // ---- copy the reflector from the owner
     const int orank = p / chunk;
-    if (!owner) {
-      const T* rv = cluster.map_shared_rank(v, orank);
-      for (int i = k + tid; i < n; i += NT) v[i] = rv[i];
-      if (tid == 0) s_scal[0] = *cluster.map_shared_rank(&s_scal[0], orank);
-    }
+    if (!owner) xc.fetch_reflector(v, &s_scal[0], tk, k, n, orank, tid, NT);
     __syncthreads();
     const T tau = s_scal[0];
     // ---- update the own remaining columns and their norms
@@ -1194,8 +1277,36 @@ __global__ void __launch_bounds__(NT, 1) k_qrcp_cluster(const QrTask<T>* tasks, 
       __syncthreads();
     }
   }
-  if (q == 0 && tid == 0) *tk.rank = rank;
-  cluster.sync();   // no CTA leaves while another may still read its shared memory
+  if (q == 0 && tid == 0) *tk.rank = ok ? rank : 0;
+  if (ok) xc.finish();
+}
+
+template <typename T, bool SMEM, int CS, int NT>
+__global__ void __launch_bounds__(NT, 1) k_qrcp_cluster(const QrTask<T>* tasks, T eps) {
+  extern __shared__ unsigned char qr_smem2[];
+  __shared__ T cand_v;
+  __shared__ int cand_i;
+  ClusterX<T, CS> xc{cooperative_groups::this_cluster(), &cand_v, &cand_i};
+  const QrTask<T> tk = tasks[blockIdx.x / CS];
+  qrcp_group<T, SMEM, NT>(tk, eps, xc, qr_smem2, &cand_v, &cand_i, nullptr);
+}
+
+// Interfaces too large for one cluster: a cooperative launch in which group t
+// (G <= QR_GMAX CTAs, one per SM) factors task t.  SMEM = true: each CTA holds
+// its column chunk in shared memory; SMEM = false: W streams from L2 / HBM,
+// spread over as many SMs as the group has CTAs.
+struct QrGroupDesc {
+  int task, q, G, pad;
+};
+
+template <typename T, bool SMEM, int NT>
+__global__ void __launch_bounds__(NT, 1) k_qrcp_group(const QrTask<T>* tasks, const QrGroupDesc* desc,
+                                                      T* prop_v, int* prop_i, GroupSync* gs, int* err, T eps) {
+  extern __shared__ unsigned char qr_smem3[];
+  const QrGroupDesc d = desc[blockIdx.x];
+  GroupX<T> xc{d.q, d.G, prop_v + (size_t)d.task * QR_GMAX, prop_i + (size_t)d.task * QR_GMAX, gs + d.task, err};
+  const QrTask<T> tk = tasks[d.task];
+  qrcp_group<T, SMEM, NT>(tk, eps, xc, qr_smem3, nullptr, nullptr, err);
 }
 
 // bytes of dynamic shared memory the SMEM variant needs for an n x c problem

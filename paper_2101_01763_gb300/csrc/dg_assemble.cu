@@ -497,8 +497,10 @@ extern "C" int dg_assemble_jacobian(const dg_mesh* mesh, int p, const double* u_
   SPAND_CUDA_TRY(cudaMemcpyAsync(d_scr, &big, sizeof(double), cudaMemcpyHostToDevice, stream));
   SPAND_CUDA_TRY(cudaMemsetAsync(d_scr + 1, 0, sizeof(double), stream));
   int* d_bad = reinterpret_cast<int*>(d_scr + 1);
+  spand::note_launch();
   k_time_step<<<(K + 127) / 128, 128, 0, stream>>>(mesh->nodes, nt, nr, p, u_hat, fl, d_scr, d_bad, T);
   const size_t smem = sizeof(Smem);
+  spand::note_launch();
   k_assemble<<<K, 256, smem, stream>>>(mesh->nodes, nt, nr, p, u_hat, fl, d_scr, A->row_ptr, rhs,
                                        A->val, d_bad, T);
   SPAND_CUDA_TRY(cudaGetLastError());

@@ -610,6 +610,7 @@ int sstep_core(const bsr_matrix* A, spand_factor_t M, const double* b, double* x
       status = SPAND_ERR_NOT_CONVERGED;
       break;
     }
+    note_launch();
     k_small<<<1, 256, 0, st>>>(S, MODE_INIT, 0, 0);
     // q0 = r / beta  (scal[1] = beta after INIT)
     status = scale_copy(N, r, Qc(0), S.scal + 1, 1, st);
@@ -638,6 +639,7 @@ int sstep_core(const bsr_matrix* A, spand_factor_t M, const double* b, double* x
         hy = {wv};
         status = gram_run(S.scal + 2, 1);
         if (status) break;
+        note_launch();
         k_small<<<1, 256, 0, st>>>(S, MODE_ARNOLDI, j, 0);
         status = scale_copy(N, wv, Qc(j + 1), S.scal + 4, 1, st);
         if (status) break;
@@ -716,6 +718,7 @@ int sstep_core(const bsr_matrix* A, spand_factor_t M, const double* b, double* x
       if (status) break;
       stl.reductions++;
       if (pend) {
+        note_launch();
         k_small<<<1, 256, 0, st>>>(S, MODE_PENDING, c, 0);
         status = check_status();
         if (status) break;
@@ -739,6 +742,7 @@ int sstep_core(const bsr_matrix* A, spand_factor_t M, const double* b, double* x
         status = block_update(N, s, s, Vc(0), N, S.S1inv, c + 1, Qc(0), N, S.CV, ldh, Pc(0), N, 0, st);
         csP = c;
       } else {
+        note_launch();
         k_small<<<1, 256, 0, st>>>(S, MODE_FIRST, c, 0);
         status = check_status();
         if (status) break;
@@ -760,6 +764,7 @@ int sstep_core(const bsr_matrix* A, spand_factor_t M, const double* b, double* x
       status = gram_run(S.G, ldg);
       if (status) break;
       stl.reductions++;
+      note_launch();
       k_small<<<1, 256, 0, st>>>(S, MODE_FLUSH, c, 0);
       status = check_status();
       if (status) break;
@@ -785,10 +790,12 @@ int sstep_core(const bsr_matrix* A, spand_factor_t M, const double* b, double* x
         }
         status = gram_run(S.G, ldg);
         if (status) break;
+        note_launch();
         k_small<<<1, 256, 0, st>>>(S, MODE_ORTH, kq, 0);
       }
     }
     // ---- x += M^-1 (Q_{0:k} y)
+    note_launch();
     k_small<<<1, 256, 0, st>>>(S, MODE_SOLVE, k_cols, 0);
     {
       // wv = Q[:, 0:k] y  via block update with no Y part: X = -Z C, C = -y

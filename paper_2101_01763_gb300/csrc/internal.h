@@ -45,6 +45,11 @@ inline void once_per_device(std::atomic<uint64_t>& done, F f) {
   done.fetch_or(bit, std::memory_order_release);
 }
 
+// Kernel launches issued by the library since it was loaded (a CUDA-graph
+// replay adds the kernels of the graph); read by spand_kernel_launches().
+extern std::atomic<uint64_t> g_kernel_launches;
+inline void note_launch(uint64_t n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
+
 // Sets the kernel's dynamic shared-memory limit to min(want, opt-in limit of
 // the device - the kernel's static shared memory) and returns the value set,
 // or -1 when a query fails.  A failing runtime call here is cleared, so it

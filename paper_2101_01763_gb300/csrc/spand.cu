@@ -14,6 +14,7 @@
 // a fixed list of gather-GEMV launches built once per factorization.
 #include <algorithm>
 #include <cmath>
+#include <chrono>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -35,6 +36,13 @@ constexpr size_t kGemvSmemMax = 200 * 1024;
 constexpr size_t kQrSmemMax = 212 * 1024;   // + <= 9 KB static stays under 227 KB
 
 // ------------------------------------------------------------------ device memory
+// host wall-clock milliseconds
+static double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+std::atomic<uint64_t> g_kernel_launches{0};
+
 void report_cuda_error(cudaError_t e, const char* expr, const char* file, int line) {
   static const bool on = [] {
     const char* v = std::getenv("SPAND_DEBUG");
@@ -44,20 +52,44 @@ void report_cuda_error(cudaError_t e, const char* expr, const char* file, int li
                        cudaGetErrorString(e));
 }
 
+// Stream-ordered device memory carved from 32 MB slabs (256-byte aligned
+// pieces), so that the thousands of small arrays of a factorization cost a
+// handful of allocator calls; large arrays get their own allocation.
 struct DevMem {
+  static constexpr size_t kSlab = size_t(32) << 20;
   std::vector<void*> ptrs;
   cudaStream_t st = nullptr;
   int err = 0;
+  char* cur = nullptr;
+  size_t left = 0;
   template <typename X>
   X* alloc(size_t n) {
     if (n == 0) n = 1;
+    const size_t bytes = (n * sizeof(X) + 255) & ~size_t(255);
     void* p = nullptr;
-    if (cudaMallocAsync(&p, n * sizeof(X), st) != cudaSuccess) {
-      err = 1;
-      return nullptr;
+    if (bytes > kSlab / 4) {
+      if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+        cudaGetLastError();
+        err = 1;
+        return nullptr;
+      }
+      ptrs.push_back(p);
+      return static_cast<X*>(p);
     }
-    ptrs.push_back(p);
-    return static_cast<X*>(p);
+    if (bytes > left) {
+      if (cudaMallocAsync(&p, kSlab, st) != cudaSuccess) {
+        cudaGetLastError();
+        err = 1;
+        return nullptr;
+      }
+      ptrs.push_back(p);
+      cur = static_cast<char*>(p);
+      left = kSlab;
+    }
+    X* r = reinterpret_cast<X*>(cur);
+    cur += bytes;
+    left -= bytes;
+    return r;
   }
   template <typename X>
   X* upload(const std::vector<X>& h) {
@@ -69,8 +101,41 @@ struct DevMem {
   void free_all() {
     for (void* p : ptrs) cudaFreeAsync(p, st);
     ptrs.clear();
+    cur = nullptr;
+    left = 0;
   }
 };
+
+struct HostPack {
+  std::vector<unsigned char> buf;
+  template <typename X>
+  size_t add(const std::vector<X>& v) {
+    const size_t off = (buf.size() + 255) & ~size_t(255);
+    buf.resize(off + std::max<size_t>(v.size(), 1) * sizeof(X));
+    if (!v.empty()) memcpy(buf.data() + off, v.data(), v.size() * sizeof(X));
+    return off;
+  }
+};
+
+// a: first array, b: second (and c: third) -- one device allocation, one copy
+template <typename A, typename B>
+static void upload2(DevMem& m, const std::vector<A>& a, const std::vector<B>& b, A*& da, B*& db) {
+  HostPack hp;
+  const size_t oa = hp.add(a), ob = hp.add(b);
+  unsigned char* d = m.upload(hp.buf);
+  da = d ? reinterpret_cast<A*>(d + oa) : nullptr;
+  db = d ? reinterpret_cast<B*>(d + ob) : nullptr;
+}
+template <typename A, typename B, typename C>
+static void upload3(DevMem& m, const std::vector<A>& a, const std::vector<B>& b, const std::vector<C>& c, A*& da,
+                    B*& db, C*& dc) {
+  HostPack hp;
+  const size_t oa = hp.add(a), ob = hp.add(b), oc = hp.add(c);
+  unsigned char* d = m.upload(hp.buf);
+  da = d ? reinterpret_cast<A*>(d + oa) : nullptr;
+  db = d ? reinterpret_cast<B*>(d + ob) : nullptr;
+  dc = d ? reinterpret_cast<C*>(d + oc) : nullptr;
+}
 
 // ------------------------------------------------------------------ launch helpers
 template <typename T>
@@ -83,10 +148,12 @@ static void launch_gemm(DevMem& tmp, const std::vector<GemmTask<T>>& tasks, cons
       for (int b = 0; b < (tasks[t].n + 63) / 64; ++b) tiles.push_back({t, a, b});
   }
   if (tiles.empty()) return;
-  auto* dt = tmp.upload(tasks);
-  auto* dm = tmp.upload(terms);
-  auto* dl = tmp.upload(tiles);
+  GemmTask<T>* dt;
+  GemmTerm<T>* dm;
+  TileItem* dl;
+  upload3(tmp, tasks, terms, tiles, dt, dm, dl);
   if (tmp.err) return;
+  note_launch();
   if constexpr (std::is_same<T, float>::value)
     k_gemm_tc<3><<<(unsigned)tiles.size(), 128, 0, st>>>(dt, dm, dl);   // FP32 factors: 3xTF32 tensor cores
   else
@@ -100,9 +167,11 @@ static void launch_copy(DevMem& tmp, const std::vector<CopyTask<T>>& tasks, cuda
     for (int a = 0; a < (tasks[t].rows + 31) / 32; ++a)
       for (int b = 0; b < (tasks[t].cols + 31) / 32; ++b) tiles.push_back({t, a, b});
   if (tiles.empty()) return;
-  auto* dt = tmp.upload(tasks);
-  auto* dl = tmp.upload(tiles);
+  CopyTask<T>* dt;
+  CopyTile* dl;
+  upload2(tmp, tasks, tiles, dt, dl);
   if (tmp.err) return;
+  note_launch();
   k_copy_tiles<T><<<(unsigned)tiles.size(), 256, 0, st>>>(dt, dl);
 }
 
@@ -134,6 +203,7 @@ static void launch_row_perm(DevMem& tmp, const std::vector<const T*>& src, const
   auto* d = tmp.upload(rows);
   auto* e = tmp.upload(cols);
   if (tmp.err) return;
+  note_launch();
   k_row_perm<T><<<(unsigned)src.size(), 256, 0, st>>>(a, b, c, d, e);
 }
 
@@ -167,9 +237,13 @@ static void batched_getrf(DevMem& tmp, std::vector<MatRef<T>>& mats, int* d_flag
   for (int k0 = 0; k0 < nmax; k0 += LU_NB) {
     if (ds && k0 < nsmall_max) {
       const size_t sm = (size_t)(nsmall_max - k0) * std::min(LU_NB, nsmall_max - k0) * sizeof(T);
+      note_launch();
       k_getrf_panel_smem<T><<<(unsigned)small.size(), 256, sm, st>>>(ds, (int)small.size(), k0, d_flags);
     }
-    if (dlg) k_getrf_panel<T><<<(unsigned)large.size(), 256, 0, st>>>(dlg, (int)large.size(), k0, d_flags);
+    if (dlg) {
+      note_launch();
+      k_getrf_panel<T><<<(unsigned)large.size(), 256, 0, st>>>(dlg, (int)large.size(), k0, d_flags);
+    }
     std::vector<GemmTask<T>> tasks;
     std::vector<GemmTerm<T>> terms;
     for (auto& m : mats) {
@@ -183,6 +257,7 @@ static void batched_getrf(DevMem& tmp, std::vector<MatRef<T>>& mats, int* d_flag
     }
     launch_gemm(tmp, tasks, terms, st);
   }
+  note_launch();
   k_ipiv_to_perm<T><<<(unsigned)mats.size(), 128, (size_t)nmax * sizeof(int), st>>>(dm, (int)mats.size());
 }
 
@@ -209,6 +284,7 @@ static void batched_inverses(DevMem& tmp, const std::vector<MatRef<T>>& mats, co
     if (tmp.err) return;
     for (size_t off = 0; off < ptr.size(); off += 65535) {
       const unsigned cnt = (unsigned)std::min<size_t>(65535, ptr.size() - off);
+      note_launch();
       k_zero_mats<T><<<dim3(32, cnt), 256, 0, st>>>(dp + off, dn + off);
     }
   }
@@ -225,6 +301,7 @@ static void batched_inverses(DevMem& tmp, const std::vector<MatRef<T>>& mats, co
   if (!dt.empty()) {
     auto* dd = tmp.upload(dt);
     if (tmp.err) return;
+    note_launch();
     k_inv_diag<T><<<(unsigned)dt.size(), 32, 0, st>>>(dd);
   }
   for (int bs = 32; bs < nmax; bs *= 2) {
@@ -277,7 +354,9 @@ static void batched_inverses(DevMem& tmp, const std::vector<MatRef<T>>& mats, co
   auto* dut = tmp.upload(ut);
   auto* dtl = tmp.upload(tiles);
   if (tmp.err) return;
+  note_launch();
   k_scale_rows<T><<<(unsigned)tiles.size(), 256, 0, st>>>(dlt, dtl);
+  note_launch();
   k_scale_cols<T><<<(unsigned)tiles.size(), 256, 0, st>>>(dut, dtl);
 }
 
@@ -295,6 +374,7 @@ static void batched_upper_inverse(DevMem& tmp, const std::vector<MatRef<T>>& mat
   auto* dut = tmp.upload(ut);
   auto* dtl = tmp.upload(tiles);
   if (tmp.err || tiles.empty()) return;
+  note_launch();
   k_inv_upper<T><<<(unsigned)tiles.size(), 256, 0, st>>>(dut, dtl);
 }
 
@@ -422,6 +502,14 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
   auto sysE0 = [&](int s) { return P.sys_elem0.empty() ? 0 : P.sys_elem0[s]; };
   auto sysDof0 = [&](int s) -> int64_t { return P.sys_dof0.empty() ? 0 : P.sys_dof0[s]; };
   auto sysK = [&](int s) { return P.sys_K.empty() ? P.K : P.sys_K[s]; };
+  const double t_begin = now_ms();
+  double t_wait = 0;
+  auto sync_st = [&]() -> cudaError_t {
+    const double t0 = now_ms();
+    const cudaError_t e = cudaStreamSynchronize(st);
+    t_wait += now_ms() - t0;
+    return e;
+  };
   F->N = (int)P.n_dof();
   F->D = D;
   F->precision = precision;
@@ -480,7 +568,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
     std::vector<int> rp(Kq + 1), col(A->nnzb);
     SPAND_CUDA_TRY(cudaMemcpyAsync(rp.data(), A->row_ptr, sizeof(int) * (Kq + 1), cudaMemcpyDeviceToHost, st));
     SPAND_CUDA_TRY(cudaMemcpyAsync(col.data(), A->col, sizeof(int) * A->nnzb, cudaMemcpyDeviceToHost, st));
-    SPAND_CUDA_TRY(cudaStreamSynchronize(st));
+    SPAND_CUDA_TRY(sync_st());
     if (rp[0] != 0 || rp[Kq] != A->nnzb) return SPAND_ERR_ARG;
     std::vector<T*> dst(A->nnzb);
     std::vector<int> ldv(A->nnzb);
@@ -498,6 +586,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
     T* const* d_dst = tmp.upload(dst);
     const int* d_ld = tmp.upload(ldv);
     if (tmp.err) return SPAND_ERR_NOMEM;
+    note_launch();
     k_level0_gather<T><<<A->nnzb, 256, 0, st>>>(A->val, nullptr, nullptr, nullptr, nullptr, d_ld, d_dst, A->nnzb, Bq);
     SPAND_CUDA_TRY(cudaGetLastError());
     tmp.free_all();
@@ -561,7 +650,17 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
     LevelRec<T>& R = recs[l];
     R.n = n;
     R.d_slots.resize(nc);
-    for (int c = 0; c < nc; ++c) R.d_slots[c] = pm.upload(slots[c]);
+    {
+      // every cluster's slot list of the level in one upload
+      std::vector<int> all;
+      std::vector<size_t> off(nc + 1, 0);
+      for (int c = 0; c < nc; ++c) off[c + 1] = off[c] + slots[c].size();
+      all.reserve(off[nc]);
+      for (int c = 0; c < nc; ++c) all.insert(all.end(), slots[c].begin(), slots[c].end());
+      int* base = pm.upload(all);
+      if (pm.err) return SPAND_ERR_NOMEM;
+      for (int c = 0; c < nc; ++c) R.d_slots[c] = base + off[c];
+    }
     DevMem tmp;
     tmp.st = st;
     // neighbour lists in the current pattern
@@ -701,6 +800,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
     if (!mats.empty()) {
       auto* dm = tmp.upload(mats);
       auto* dd = tmp.upload(dsc_mut);
+      note_launch();
       k_diag_sqrt<T><<<(unsigned)mats.size(), 128, 0, st>>>(dm, dd, (int)mats.size());
     }
     batched_inverses(tmp, mats, SL, SU, dsc, st);
@@ -771,6 +871,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
     if (tmp.err) return SPAND_ERR_NOMEM;
     launch_copy(tmp, cps, st);
     std::vector<int> rank(qt.size());
+    int qf[4] = {0, 0, 0, 0};
     if (!qt.empty()) {
       // reflector storage must be zero above the diagonal for the WY products
       for (auto& q : qt) SPAND_CUDA_TRY(cudaMemsetAsync(q.V, 0, sizeof(T) * (size_t)q.n * std::min(q.n, q.c), st));
@@ -812,7 +913,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       const int cl16 = (cur_dev >= 0 && cur_dev < 64 && ((can16.load() >> cur_dev) & 1)) ? 1 : 0;
       // on-chip variants: chunk resident in shared memory with 8 or 16 CTAs;
       // the rest streams W from L2 / HBM
-      std::vector<QrTask<T>> q_sm8, q_sm16, q_gl;
+      std::vector<QrTask<T>> q_sm8, q_sm16, q_gl, q_big;
       size_t sm8_max = 0, sm16_max = 0, gl_max = 0;
       // what each on-chip kernel can be given next to its static shared memory
       const long long lim8 = set_dyn_smem((const void*)k_qrcp_cluster<T, true, QR_CS, QR_THREADS>, kQrSmemMax);
@@ -828,10 +929,99 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
           q_sm16.push_back(qt[k]);
           sm16_max = std::max(sm16_max, b16);
         } else {
-          q_gl.push_back(qt[k]);
-          gl_max = std::max(gl_max, ((size_t)qt[k].n + 31) * sizeof(T));
+          q_big.push_back(qt[k]);
         }
       }
+      // too large for one cluster: CTA groups of cooperative launches, as many
+      // groups per launch as fit on the GPU at once.  A group keeps W in
+      // shared memory when its chunks fit (G <= the resident-CTA capacity);
+      // otherwise W streams from L2 / HBM through a group sized to the problem.
+      struct CoopLaunch {
+        std::vector<QrGroupDesc> desc;
+        size_t bytes = 0;
+        bool smem = true;
+      };
+      std::vector<CoopLaunch> coop;
+      std::vector<QrTask<T>> q_coop;
+      int n_group_smem = 0, n_group_stream = 0;
+      if (!q_big.empty()) {
+        auto kg = k_qrcp_group<T, true, QR_THREADS>;
+        auto ks = k_qrcp_group<T, false, 1024>;
+        const long long limg = set_dyn_smem((const void*)kg, kQrSmemMax);
+        const long long lims = set_dyn_smem((const void*)ks, kQrSmemMax);
+        int dev = 0, nsm = 0, coop_ok = 0, per_sm = 0, per_sm_s = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&coop_ok, cudaDevAttrCooperativeLaunch, dev);
+        if (limg > 0 && coop_ok &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kg, QR_THREADS, (size_t)limg) != cudaSuccess)
+          per_sm = 0;
+        if (lims > 0 && coop_ok &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, ks, 1024, (size_t)lims) != cudaSuccess)
+          per_sm_s = 0;
+        cudaGetLastError();
+        const int cap = std::min(QR_GMAX, coop_ok ? per_sm * nsm : 0);
+        const int cap_s = std::min(QR_GMAX, coop_ok ? per_sm_s * nsm : 0);
+        std::vector<std::pair<int, int>> in_smem, streamed;   // (task index in q_coop, G)
+        for (auto& t : q_big) {
+          int G = 2;
+          while (G <= cap && (long long)qrcp_smem_bytes<T>(t.n, t.c, G) > limg) ++G;
+          if (G <= cap && limg > 0) {
+            in_smem.push_back({(int)q_coop.size(), G});
+            q_coop.push_back(t);
+          } else if (cap_s >= 16) {
+            // about 1 MB of W per CTA, at least 16 CTAs, at most the resident capacity
+            const double mb = (double)t.n * t.c * sizeof(T) / (1 << 20);
+            const int Gs = std::max(16, std::min(cap_s, (int)std::ceil(mb)));
+            streamed.push_back({(int)q_coop.size(), Gs});
+            q_coop.push_back(t);
+          } else {
+            q_gl.push_back(t);
+            gl_max = std::max(gl_max, ((size_t)t.n + 31) * sizeof(T));
+          }
+        }
+        auto pack = [&](const std::vector<std::pair<int, int>>& v, bool smem, int capk) {
+          CoopLaunch cur;
+          cur.smem = smem;
+          int used = 0;
+          for (auto& pr : v) {
+            const QrTask<T>& t = q_coop[pr.first];
+            const int G = pr.second;
+            if (used + G > capk && !cur.desc.empty()) {
+              coop.push_back(cur);
+              cur = CoopLaunch();
+              cur.smem = smem;
+              used = 0;
+            }
+            for (int g = 0; g < G; ++g) cur.desc.push_back({pr.first, g, G, 0});
+            cur.bytes = std::max(cur.bytes, smem ? qrcp_smem_bytes<T>(t.n, t.c, G) : ((size_t)t.n + 31) * sizeof(T));
+            used += G;
+          }
+          if (!cur.desc.empty()) coop.push_back(cur);
+        };
+        pack(in_smem, true, cap);
+        pack(streamed, false, cap_s);
+        n_group_smem = (int)in_smem.size();
+        n_group_stream = (int)streamed.size();
+      }
+      T* d_prop_v = nullptr;
+      int* d_prop_i = nullptr;
+      GroupSync* d_gs = nullptr;
+      QrTask<T>* d_coop = nullptr;
+      std::vector<QrGroupDesc*> d_desc;
+      if (!q_coop.empty()) {
+        d_coop = tmp.upload(q_coop);
+        d_prop_v = tmp.alloc<T>(q_coop.size() * QR_GMAX);
+        d_prop_i = tmp.alloc<int>(q_coop.size() * QR_GMAX);
+        d_gs = tmp.alloc<GroupSync>(q_coop.size());
+        for (auto& cl : coop) d_desc.push_back(tmp.upload(cl.desc));
+        if (tmp.err) return SPAND_ERR_NOMEM;
+        SPAND_CUDA_TRY(cudaMemsetAsync(d_gs, 0, sizeof(GroupSync) * q_coop.size(), st));
+      }
+      qf[0] = (int)q_sm8.size();
+      qf[1] = (int)q_sm16.size();
+      qf[2] = n_group_smem;
+      qf[3] = n_group_stream + (int)q_gl.size();
       // task arrays are uploaded on st before the fork, so the side stream
       // never reads them ahead of their copies
       QrTask<T>* d_gl = q_gl.empty() ? nullptr : tmp.upload(q_gl);
@@ -855,6 +1045,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
+        note_launch();
         SPAND_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, dq, (T)eps));
         return SPAND_OK;
       };
@@ -872,20 +1063,58 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
                           k_qrcp_cluster<T, true, QR_CS, QR_THREADS>));
       SPAND_CUDA_TRY(cudaEventRecord(join_ev, side));
       SPAND_CUDA_TRY(cudaStreamWaitEvent(st, join_ev, 0));
+      // cooperative CTA groups after the join, so that nothing else holds SMs
+      // while a launch that needs all of its CTAs resident at once starts
+      {
+        for (size_t li = 0; li < coop.size(); ++li) {
+          const void* kfn = coop[li].smem ? (const void*)k_qrcp_group<T, true, QR_THREADS>
+                                          : (const void*)k_qrcp_group<T, false, 1024>;
+          if (set_dyn_smem(kfn, coop[li].bytes) < (long long)coop[li].bytes) return SPAND_ERR_UNSUPPORTED;
+          cudaLaunchConfig_t cfg = {};
+          cfg.gridDim = dim3((unsigned)coop[li].desc.size(), 1, 1);
+          cfg.blockDim = dim3(coop[li].smem ? QR_THREADS : 1024, 1, 1);
+          cfg.dynamicSmemBytes = coop[li].bytes;
+          cfg.stream = st;
+          cudaLaunchAttribute attr[1];
+          attr[0].id = cudaLaunchAttributeCooperative;
+          attr[0].val.cooperative = 1;
+          cfg.attrs = attr;
+          cfg.numAttrs = 1;
+          note_launch();
+          const QrTask<T>* a0 = d_coop;
+          const QrGroupDesc* a1 = d_desc[li];
+          if (coop[li].smem)
+            SPAND_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_qrcp_group<T, true, QR_THREADS>, a0, a1, d_prop_v, d_prop_i,
+                                              d_gs, d_flags, (T)eps));
+          else
+            SPAND_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_qrcp_group<T, false, 1024>, a0, a1, d_prop_v, d_prop_i, d_gs,
+                                              d_flags, (T)eps));
+        }
+      }
       ev_end(ev_qr[l]);
       S.rrqr_launches += 1;
       SPAND_CUDA_TRY(cudaMemcpyAsync(rank.data(), d_rank, sizeof(int) * qt.size(), cudaMemcpyDeviceToHost, st));
     }
     int hflags[4];
     SPAND_CUDA_TRY(cudaMemcpyAsync(hflags, d_flags, sizeof(hflags), cudaMemcpyDeviceToHost, st));
-    SPAND_CUDA_TRY(cudaStreamSynchronize(st));
+    SPAND_CUDA_TRY(sync_st());
     if (hflags[0] & 1) return SPAND_ERR_ZERO_PIVOT;   // the root cause when both are set
     if (hflags[0] & 2) return SPAND_ERR_NONFINITE;
-    S.t_rrqr_ms += ev_read(ev_qr[l]);
+    if (hflags[0] & 16) {
+      report_cuda_error(cudaErrorLaunchTimeout, "RRQR group barrier", __FILE__, __LINE__);
+      return SPAND_ERR_CUDA;                          // a group barrier ran out of time
+    }
+    S.t_rrqr_level_ms[l] = ev_read(ev_qr[l]);
+    S.t_rrqr_ms += S.t_rrqr_level_ms[l];
     S.t_elim_gemm_ms += ev_read(ev_gm[l]);
     for (size_t q = 0; q < qt.size(); ++q)
       for (int k = 0; k < rank[q]; ++k)
-        S.rrqr_bytes += 2.0 * (double)(qt[q].n - k) * (double)(qt[q].c - k) * sizeof(T);
+        S.rrqr_bytes_level[l] += 2.0 * (double)(qt[q].n - k) * (double)(qt[q].c - k) * sizeof(T);
+    S.rrqr_bytes += S.rrqr_bytes_level[l];
+    S.rrqr_form_count[l][0] = qf[0];
+    S.rrqr_form_count[l][1] = qf[1];
+    S.rrqr_form_count[l][2] = qf[2];
+    S.rrqr_form_count[l][3] = qf[3];
     std::vector<int> r(nc, 0);
     std::vector<char> spars(nc, 0);
     std::vector<T*> Qc(nc, nullptr);
@@ -944,10 +1173,12 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       launch_gemm(tmp, gt, gm, st);
       if (!wy.empty()) {
         auto* dw = tmp.upload(wy);
+        note_launch();
         k_wy_tinv<T><<<(unsigned)wy.size(), 256, 0, st>>>(dw);
         // T = (T^-1)^-1 with the batched upper-triangular inverse
         batched_upper_inverse(tmp, tri, Tinv, st);
         auto* de = tmp.upload(eye_q);
+        note_launch();
         k_eye<T><<<std::min<unsigned>((unsigned)eye_q.size(), 1024), 128, 0, st>>>(de, (int)eye_q.size());
       }
       launch_gemm(tmp, mt, mm, st);
@@ -1019,6 +1250,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
     launch_gemm(tmp, t2, m2, st);
     if (!eyes.empty()) {
       auto* de = tmp.upload(eyes);
+      note_launch();
       k_eye<T><<<std::min<unsigned>((unsigned)eyes.size(), 1024), 128, 0, st>>>(de, (int)eyes.size());
     }
     SPAND_CUDA_TRY(cudaGetLastError());
@@ -1033,7 +1265,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
   {
     int hflags[4];
     SPAND_CUDA_TRY(cudaMemcpyAsync(hflags, d_flags, sizeof(hflags), cudaMemcpyDeviceToHost, st));
-    SPAND_CUDA_TRY(cudaStreamSynchronize(st));
+    SPAND_CUDA_TRY(sync_st());
     S.t_elim_gemm_ms += ev_read(ev_gm[D]);
     if (hflags[0] & 1) return SPAND_ERR_ZERO_PIVOT;   // the root cause when both are set
     if (hflags[0] & 2) return SPAND_ERR_NONFINITE;
@@ -1069,6 +1301,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       tmpp.st = st;
       auto* dpt = tmpp.upload(pt);
       if (tmpp.err) return SPAND_ERR_NOMEM;
+      note_launch();
       k_perm_slots<<<(unsigned)pt.size(), 256, 0, st>>>(dpt);
       tmpp.free_all();
     }
@@ -1081,9 +1314,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       for (int r0 = 0; r0 < tasks[t].m; r0 += GV_ROWS) tiles.push_back({t, r0});
     for (auto& tm : terms) ph.kmax = std::max(ph.kmax, tm.k);
     if (tiles.empty()) return ph;
-    ph.tasks = pm.upload(tasks);
-    ph.terms = pm.upload(terms);
-    ph.tiles = pm.upload(tiles);
+    upload3(pm, tasks, terms, tiles, ph.tasks, ph.terms, ph.tiles);
     ph.ntiles = (int)tiles.size();
     return ph;
   };
@@ -1293,9 +1524,11 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
     }
 
   S.factor_bytes = F->progs[0]->bytes;
+  S.t_host_ms = now_ms() - t_begin;
+  S.t_wait_ms = t_wait;
   if (pm.err) return SPAND_ERR_NOMEM;
   SPAND_CUDA_TRY(cudaGetLastError());
-  SPAND_CUDA_TRY(cudaStreamSynchronize(st));
+  SPAND_CUDA_TRY(sync_st());
   return SPAND_OK;
 }
 
@@ -1313,8 +1546,9 @@ static void gemv_attr() {
 }
 
 template <typename T>
-static int run_phases(const std::vector<typename ApplyProg<T>::Phase>& ph, cudaStream_t st) {
+static int run_phases(const std::vector<typename ApplyProg<T>::Phase>& ph, cudaStream_t st, bool capturing = false) {
   gemv_attr<T>();
+  if (!capturing) note_launch(ph.size());
   for (auto& p : ph) {
     const size_t sm = (size_t)std::max(p.kmax, 1) * sizeof(T);
     k_gemv<T><<<p.ntiles, 256, sm, st>>>(p.tasks, p.terms, p.tiles);
@@ -1331,6 +1565,7 @@ int apply_impl(FactorT<T>* F, Program<T>& pg, const double* r, double* zout, int
   const int N = pg.N;
   T* w = F->w + pg.off;
   const unsigned g = (unsigned)std::max(1, std::min(4096, (N + 255) / 256));
+  note_launch();
   k_convert<double, T><<<g, 256, 0, st>>>(r, w, N);
   const int d = transpose ? 1 : 0;
   const auto& fwd = transpose ? pg.prog.tfwd : pg.prog.fwd;
@@ -1349,8 +1584,8 @@ int apply_impl(FactorT<T>* F, Program<T>& pg, const double* r, double* zout, int
       cudaGraph_t graph = nullptr;
       bool ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
       if (ok) {
-        run_phases<T>(fwd, cap);
-        run_phases<T>(bwd, cap);
+        run_phases<T>(fwd, cap, true);
+        run_phases<T>(bwd, cap, true);
         ok = cudaStreamEndCapture(cap, &graph) == cudaSuccess && graph;
       }
       if (ok) ok = cudaGraphInstantiate(&pg.graph[d], graph, 0) == cudaSuccess;
@@ -1360,12 +1595,14 @@ int apply_impl(FactorT<T>* F, Program<T>& pg, const double* r, double* zout, int
       if (!ok) pg.graph[d] = nullptr;
     }
     if (pg.graph[d]) {
+      note_launch(fwd.size() + bwd.size());
       SPAND_CUDA_TRY(cudaGraphLaunch(pg.graph[d], st));
     } else {
       run_phases<T>(fwd, st);
       run_phases<T>(bwd, st);
     }
   }
+  note_launch();
   k_convert<T, double><<<g, 256, 0, st>>>(w, zout, N);
   SPAND_CUDA_TRY(cudaGetLastError());
   return SPAND_OK;
@@ -1503,9 +1740,14 @@ int spand_factor_stats(spand_factor_t F, spand_stats* st) {
     st->t_elim_gemm_ms = B.stats.t_elim_gemm_ms;
     st->elim_gemm_flops = B.stats.elim_gemm_flops;
     st->elim_gemm_launches = B.stats.elim_gemm_launches;
+    memcpy(st->t_rrqr_level_ms, B.stats.t_rrqr_level_ms, sizeof(st->t_rrqr_level_ms));
+    memcpy(st->rrqr_bytes_level, B.stats.rrqr_bytes_level, sizeof(st->rrqr_bytes_level));
+    memcpy(st->rrqr_form_count, B.stats.rrqr_form_count, sizeof(st->rrqr_form_count));
   }
   return SPAND_OK;
 }
+
+uint64_t spand_kernel_launches(void) { return spand::g_kernel_launches.load(); }
 
 int spand_apply(spand_factor_t F, const double* r, double* z, int transpose, cudaStream_t stream) {
   if (!F || !r || !z || r == z) return SPAND_ERR_ARG;

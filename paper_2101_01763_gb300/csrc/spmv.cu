@@ -72,6 +72,7 @@ int spmv_fused(const bsr_matrix* A, const double* x, double* y, int transpose, d
                const double* u1, double a2, const double* u2, cudaStream_t st) {
   const int64_t n = (int64_t)A->K * A->B;
   const unsigned g = (unsigned)((n + 255) / 256);
+  note_launch();
   if (!transpose)
     k_bsr_spmv<<<g, 256, 0, st>>>(A->K, A->B, A->row_ptr, A->col, A->val, x, y, sa, a1, u1, a2, u2);
   else
@@ -136,7 +137,9 @@ __global__ void k_gram_reduce(int nblk, int nz, int ny, const double* part, doub
 int gram(int64_t N, int nz, const double* const* dZ, int ny, const double* const* dY, double* part, int nblk,
          double* G, int ldg, cudaStream_t st) {
   if (ny > 32 || nz <= 0 || ny <= 0) return SPAND_ERR_ARG;
+  note_launch();
   k_gram_partial<<<nblk, 256, 0, st>>>(N, nz, dZ, ny, dY, part);
+  note_launch();
   k_gram_reduce<<<(nz * ny + 127) / 128, 128, 0, st>>>(nblk, nz, ny, part, G, ldg);
   return cudaGetLastError() == cudaSuccess ? SPAND_OK : SPAND_ERR_CUDA;
 }
@@ -187,6 +190,7 @@ int block_update(int64_t N, int s, int ny, const double* Y, int64_t ldy, const d
   static std::atomic<uint64_t> attr{0};
   once_per_device(attr, [] { set_dyn_smem((const void*)k_block_update, 200 * 1024); });
   const unsigned g = (unsigned)std::min<int64_t>(152 * 8, (N + 255) / 256);
+  note_launch();
   k_block_update<<<g, 256, sm, st>>>(N, s, ny, Y, ldy, Sinv, nz, Z, ldz, C, ldc, X, ldx, accumulate);
   return cudaGetLastError() == cudaSuccess ? SPAND_OK : SPAND_ERR_CUDA;
 }
@@ -199,6 +203,7 @@ __global__ void k_scale_copy(int64_t N, const double* a, double* b, const double
 
 int scale_copy(int64_t N, const double* a, double* b, const double* scal, int invert, cudaStream_t st) {
   const unsigned g = (unsigned)std::min<int64_t>(152 * 8, (N + 255) / 256);
+  note_launch();
   k_scale_copy<<<g, 256, 0, st>>>(N, a, b, scal, invert);
   return cudaGetLastError() == cudaSuccess ? SPAND_OK : SPAND_ERR_CUDA;
 }
@@ -211,6 +216,7 @@ __global__ void k_axpy_dev(int64_t N, const double* coef, double sign, const dou
 
 int axpy_dev(int64_t N, const double* coef, double sign, const double* x, double* y, cudaStream_t st) {
   const unsigned g = (unsigned)std::min<int64_t>(152 * 8, (N + 255) / 256);
+  note_launch();
   k_axpy_dev<<<g, 256, 0, st>>>(N, coef, sign, x, y);
   return cudaGetLastError() == cudaSuccess ? SPAND_OK : SPAND_ERR_CUDA;
 }
@@ -239,6 +245,7 @@ __global__ void __launch_bounds__(256) k_pattern_outer(int K, int B, const int* 
 extern "C" int bsr_pattern_outer(const bsr_matrix* A, const double* u, const double* v, double alpha, double* out,
                                  cudaStream_t stream) {
   if (!A || !u || !v || !out || !A->row_ptr || !A->col || A->K <= 0 || A->B <= 0) return SPAND_ERR_ARG;
+  spand::note_launch();
   spand::k_pattern_outer<<<A->K, 256, 0, stream>>>(A->K, A->B, A->row_ptr, A->col, u, v, alpha, out);
   return cudaGetLastError() == cudaSuccess ? SPAND_OK : SPAND_ERR_CUDA;
 }
