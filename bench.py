@@ -448,6 +448,9 @@ def main():
         "factor_ms": statistics.mean(a for a, _ in ev_mx), "solve_ms": statistics.mean(b for _, b in ev_mx),
         "fp64_factor_ms": statistics.mean(a for a, _ in ev_64), "fp64_solve_ms": statistics.mean(b for _, b in ev_64),
         "gmres_iters_mixed": gst_mx["iters"], "gmres_iters_fp64": gst_64["iters"],
+        "factor_host_ms": fst_mx["t_host_ms"], "factor_gpu_wait_ms": fst_mx["t_wait_ms"],
+        "factor_host_phase_ms": fst_mx["t_host_phase_ms"],
+        "rrqr_ms_per_level": fst_mx["t_rrqr_level_ms"], "rrqr_forms_per_level": fst_mx["rrqr_form_count"],
         "true_relres_mixed": relres, "ranks_per_level": fst_mx["sum_r"],
         "solves_per_s": world * 1e3 / t_mx,
         "e2e": {"value": t_e2e, "unit": "ms", "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},

@@ -205,6 +205,12 @@ typedef struct {
    * the difference is host work (planning, task tables, allocations).      */
   double t_host_ms;
   double t_wait_ms;
+  /* the host wall time split by phase (summed over levels): [0] level setup
+   * and last-level tail, [1] elimination, [2] scaling, [3] RRQR set-up and
+   * launch, [4] wait for the level's ranks, [5] Q_c formation, [6] merge
+   * into the next level (and the root elimination with the final check),
+   * [7] apply programs                                                      */
+  double t_host_phase_ms[8];
 } spand_stats;
 int spand_factor_stats(spand_factor_t F, spand_stats* st);
 

@@ -45,7 +45,8 @@ class SpandStats(C.Structure):
                 ("t_rrqr_ms", C.c_double), ("rrqr_bytes", C.c_double), ("rrqr_launches", C.c_int),
                 ("t_elim_gemm_ms", C.c_double), ("elim_gemm_flops", C.c_double), ("elim_gemm_launches", C.c_int),
                 ("t_rrqr_level_ms", C.c_double * 32), ("rrqr_bytes_level", C.c_double * 32),
-                ("rrqr_form_count", (C.c_int * 4) * 32), ("t_host_ms", C.c_double), ("t_wait_ms", C.c_double)]
+                ("rrqr_form_count", (C.c_int * 4) * 32), ("t_host_ms", C.c_double), ("t_wait_ms", C.c_double),
+                ("t_host_phase_ms", C.c_double * 8)]
 
 
 class GmresOpts(C.Structure):

@@ -173,7 +173,7 @@ class Factor:
                     elim_gemm_launches=s.elim_gemm_launches, t_rrqr_level_ms=list(s.t_rrqr_level_ms[:n]),
                     rrqr_bytes_level=list(s.rrqr_bytes_level[:n]),
                     rrqr_form_count=[list(s.rrqr_form_count[l]) for l in range(n)],
-                    t_host_ms=s.t_host_ms, t_wait_ms=s.t_wait_ms)
+                    t_host_ms=s.t_host_ms, t_wait_ms=s.t_wait_ms, t_host_phase_ms=list(s.t_host_phase_ms))
 
     def close(self):
         if getattr(self, "h", None):

@@ -1100,8 +1100,30 @@ struct GroupX {
   __device__ void finish() {}
 };
 
+// argmax over the 32 lanes of a warp (largest value, lowest index on ties)
+template <typename T>
+__device__ inline void warp_argmax(T& v, int& i) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const T v2 = __shfl_xor_sync(0xffffffffu, v, o);
+    const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
+    argmax_pair(v, i, v2, i2);
+  }
+}
+
+// sum over aligned groups of L lanes (L a power of two <= 32)
+template <typename T>
+__device__ inline T group_sum(T x, int L) {
+  for (int o = L >> 1; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
 // The factorization of one interface by the CTAs of one exchange group X
-// (rank q of X.size() CTAs; columns split in contiguous chunks).
+// (rank q of X.size() CTAs; columns split in contiguous chunks).  Inside a
+// CTA a column is handled by L consecutive lanes of one warp (L chosen so
+// that one pass covers the chunk), which combine their row partial sums with
+// shuffles: the column pass of a pivot step needs no block barrier, and it
+// also yields the CTA's proposal for the next step.
 template <typename T, bool SMEM, int NT, typename X>
 __device__ void qrcp_group(const QrTask<T>& tk, T eps, X& xc, unsigned char* smem_raw, T* cand_v, int* cand_i,
                            int* err) {
@@ -1113,18 +1135,18 @@ __device__ void qrcp_group(const QrTask<T>& tk, T eps, X& xc, unsigned char* sme
   __shared__ int allc_i[CSM];
   __shared__ T s_scal[4];                          // [0] tau, [1] winner norm^2
   __shared__ int s_win;
-  __shared__ T part[NT];                           // (segment, column) partials
-  __shared__ T dotv[NT];
+  __shared__ T s_prop_v;                           // this CTA's proposal for the next step
+  __shared__ int s_prop_i;
   const int q = xc.rank(), CS = xc.size();
   const int n = tk.n, c = tk.c;
   const int chunk = (c + CS - 1) / CS;
   const int j0 = min(c, q * chunk), j1 = min(c, j0 + chunk);
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int wdt = j1 - j0;
-  const int CW = max(32, min(NT, (wdt + 31) / 32 * 32));   // columns per group
-  const int SEG = NT / CW;                                   // row segments
-  const int cl = tid % CW, seg = tid / CW;
-  const bool in_grid = seg < SEG;
+  int L = 1;                                       // lanes per column
+  while (L < 32 && (NT / (2 * L)) >= wdt) L *= 2;
+  const int slots = NT / L;                        // columns per pass
+  const int cs_ = tid / L, li = tid % L;
   T* Wg = tk.W;
   T* Ws = v + ((n + 31) & ~31);
   const size_t ldg = (size_t)c;
@@ -1140,34 +1162,33 @@ __device__ void qrcp_group(const QrTask<T>& tk, T eps, X& xc, unsigned char* sme
     __syncthreads();
   }
   // ---- initial column norms
-  for (int g = j0; g < j1; g += CW) {
-    const int j = g + cl;
-    T s = 0;
-    if (in_grid && j < j1)
-      for (int i = seg; i < n; i += SEG) {
+  for (int g = j0; g < j1; g += slots) {
+    const int j = g + cs_;
+    T sum = 0;
+    if (j < j1)
+      for (int i = li; i < n; i += L) {
         const T a = at(i, j);
-        s += a * a;
+        sum += a * a;
       }
-    part[tid] = s;
-    __syncthreads();
-    if (seg == 0 && j < j1) {
-      T t = 0;
-      for (int r = 0; r < SEG; ++r) t += part[r * CW + cl];
-      tk.norm2[j] = t;
-    }
-    __syncthreads();
+    sum = group_sum(sum, L);
+    if (li == 0 && j < j1) tk.norm2[j] = sum;
   }
+  __syncthreads();
   const int kmax = min(n, c);
   int rank = kmax;
   T nrm0 = 0;
   bool ok = true;
   for (int k = 0; k < kmax; ++k) {
-    // ---- local proposal
-    T best = -1;
-    int bi = c;
-    for (int j = j0 + tid; j < j1; j += NT) argmax_pair(best, bi, tk.norm2[j], j);
-    block_argmax(best, bi, red_v, red_i);
-    if (tid == 0) xc.publish(best, bi);
+    // ---- this CTA's proposal (from the norms at k = 0, else from the last column pass)
+    if (k == 0) {
+      T best = -1;
+      int bi = c;
+      for (int j = j0 + tid; j < j1; j += NT) argmax_pair(best, bi, tk.norm2[j], j);
+      block_argmax(best, bi, red_v, red_i);
+      if (tid == 0) xc.publish(best, bi);
+    } else if (tid == 0) {
+      xc.publish(s_prop_v, s_prop_i);
+    }
     if (!(ok = xc.sync())) break;
     // ---- group-wide winner: one read per thread, in parallel
     if (tid < CS) xc.gather(tid, allc_v[tid], allc_i[tid]);
@@ -1228,36 +1249,30 @@ __device__ void qrcp_group(const QrTask<T>& tk, T eps, X& xc, unsigned char* sme
     if (!owner) xc.fetch_reflector(v, &s_scal[0], tk, k, n, orank, tid, NT);
     __syncthreads();
     const T tau = s_scal[0];
-    // ---- update the own remaining columns and their norms
-    for (int g = j0; g < j1; g += CW) {
-      const int j = g + cl;
-      const bool act = in_grid && j < j1 && tk.norm2[j] >= 0;
+    // ---- update the own remaining columns and their norms; track the best
+    T best = -1;
+    int bi = c;
+    for (int g = j0; g < j1; g += slots) {
+      const int j = g + cs_;
+      const bool act = j < j1 && tk.norm2[j] >= 0;
       T d0 = 0, d1 = 0;
       if (act) {
-        int i = k + seg;
-        for (; i + SEG < n; i += 2 * SEG) {
+        int i = k + li;
+        for (; i + L < n; i += 2 * L) {
           d0 += v[i] * at(i, j);
-          d1 += v[i + SEG] * at(i + SEG, j);
+          d1 += v[i + L] * at(i + L, j);
         }
         if (i < n) d0 += v[i] * at(i, j);
       }
-      part[tid] = d0 + d1;
-      __syncthreads();
-      if (seg == 0) {
-        T t = 0;
-        for (int r = 0; r < SEG; ++r) t += part[r * CW + cl];
-        dotv[cl] = t * tau;
-      }
-      __syncthreads();
+      const T dt = group_sum(d0 + d1, L) * tau;
       T s0 = 0;
       if (act) {
-        const T dt = dotv[cl];
-        int i = k + seg;
-        for (; i + SEG < n; i += 2 * SEG) {
+        int i = k + li;
+        for (; i + L < n; i += 2 * L) {
           T& a = at(i, j);
-          T& b = at(i + SEG, j);
+          T& b = at(i + L, j);
           a -= dt * v[i];
-          b -= dt * v[i + SEG];
+          b -= dt * v[i + L];
           if (i > k) s0 += a * a;
           s0 += b * b;
         }
@@ -1267,14 +1282,24 @@ __device__ void qrcp_group(const QrTask<T>& tk, T eps, X& xc, unsigned char* sme
           if (i > k) s0 += a * a;
         }
       }
-      part[tid] = s0;
-      __syncthreads();
-      if (seg == 0 && j < j1 && tk.norm2[j] >= 0) {
-        T t = 0;
-        for (int r = 0; r < SEG; ++r) t += part[r * CW + cl];
-        tk.norm2[j] = t;
+      s0 = group_sum(s0, L);
+      if (li == 0 && act) {
+        tk.norm2[j] = s0;
+        argmax_pair(best, bi, s0, j);
       }
-      __syncthreads();
+    }
+    warp_argmax(best, bi);
+    if (lane == 0) {
+      red_v[wid] = best;
+      red_i[wid] = bi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      T b2 = -1;
+      int i2 = c;
+      for (int w = 0; w < NT / 32; ++w) argmax_pair(b2, i2, red_v[w], red_i[w]);
+      s_prop_v = b2;
+      s_prop_i = i2;
     }
   }
   if (q == 0 && tid == 0) *tk.rank = ok ? rank : 0;

@@ -19,6 +19,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <memory>
 #include <new>
 #include <type_traits>
@@ -33,7 +34,7 @@ namespace spand {
 // largest dynamic shared memory any kernel here asks for (x vectors, reflectors)
 constexpr size_t kGemvSmemMax = 200 * 1024;
 // dynamic shared memory of the RRQR cluster kernel (W chunk + reflector)
-constexpr size_t kQrSmemMax = 212 * 1024;   // + <= 9 KB static stays under 227 KB
+constexpr size_t kQrSmemMax = 224 * 1024;   // clamped per kernel to the opt-in limit minus its static shared memory
 
 // ------------------------------------------------------------------ device memory
 // host wall-clock milliseconds
@@ -52,6 +53,83 @@ void report_cuda_error(cudaError_t e, const char* expr, const char* file, int li
                        cudaGetErrorString(e));
 }
 
+// Pinned host staging for the small uploads of a factorization (task tables,
+// slot lists): a copy from pinned memory is a plain DMA enqueue, where a copy
+// from pageable memory is staged by the driver on every call.  The chunks come
+// from a process-wide pool; a stage is reset only after its stream has been
+// synchronised, so no queued copy still reads a reused chunk.
+struct PinnedPool {
+  std::mutex mu;
+  std::vector<std::pair<char*, size_t>> free_chunks;
+  static PinnedPool& get() {
+    static PinnedPool* p = new PinnedPool();   // never destroyed: outlives every factor
+    return *p;
+  }
+  std::pair<char*, size_t> take(size_t want) {
+    {
+      std::lock_guard<std::mutex> g(mu);
+      for (size_t i = 0; i < free_chunks.size(); ++i)
+        if (free_chunks[i].second >= want) {
+          auto c = free_chunks[i];
+          free_chunks.erase(free_chunks.begin() + i);
+          return c;
+        }
+    }
+    void* h = nullptr;
+    if (cudaMallocHost(&h, want) != cudaSuccess) {
+      cudaGetLastError();
+      return {nullptr, 0};
+    }
+    return {static_cast<char*>(h), want};
+  }
+  void give(std::pair<char*, size_t> c) {
+    std::lock_guard<std::mutex> g(mu);
+    free_chunks.push_back(c);
+  }
+};
+
+struct PinnedStage {
+  static constexpr size_t kChunk = size_t(8) << 20;
+  std::vector<std::pair<char*, size_t>> chunks;
+  size_t ci = 0, off = 0;
+  // host buffer for `bytes`, or nullptr (the caller then copies from pageable memory)
+  char* get(size_t bytes) {
+    bytes = (bytes + 63) & ~size_t(63);
+    while (true) {
+      if (ci < chunks.size() && off + bytes <= chunks[ci].second) {
+        char* p = chunks[ci].first + off;
+        off += bytes;
+        return p;
+      }
+      if (ci < chunks.size() && off > 0) {
+        ++ci;
+        off = 0;
+        continue;
+      }
+      if (ci >= chunks.size()) {
+        auto c = PinnedPool::get().take(std::max(kChunk, bytes));
+        if (!c.first) return nullptr;
+        chunks.push_back(c);
+        ci = chunks.size() - 1;
+        off = 0;
+        continue;
+      }
+      // current chunk is empty but too small: take a larger one after it
+      auto c = PinnedPool::get().take(std::max(kChunk, bytes));
+      if (!c.first) return nullptr;
+      chunks.insert(chunks.begin() + ci, c);
+      off = 0;
+    }
+  }
+  void reset() {   // only after the stream that read the chunks has been synchronised
+    ci = 0;
+    off = 0;
+  }
+  ~PinnedStage() {
+    for (auto& c : chunks) PinnedPool::get().give(c);
+  }
+};
+
 // Stream-ordered device memory carved from 32 MB slabs (256-byte aligned
 // pieces), so that the thousands of small arrays of a factorization cost a
 // handful of allocator calls; large arrays get their own allocation.
@@ -62,6 +140,7 @@ struct DevMem {
   int err = 0;
   char* cur = nullptr;
   size_t left = 0;
+  PinnedStage* stage = nullptr;   // optional pinned staging for uploads
   template <typename X>
   X* alloc(size_t n) {
     if (n == 0) n = 1;
@@ -94,8 +173,17 @@ struct DevMem {
   template <typename X>
   X* upload(const std::vector<X>& h) {
     X* d = alloc<X>(h.size());
-    if (d && !h.empty() && cudaMemcpyAsync(d, h.data(), h.size() * sizeof(X), cudaMemcpyHostToDevice, st) != cudaSuccess)
-      err = 1;
+    if (!d || h.empty()) return d;
+    const size_t bytes = h.size() * sizeof(X);
+    const void* src = h.data();
+    if (stage) {
+      char* p = stage->get(bytes);
+      if (p) {
+        memcpy(p, h.data(), bytes);
+        src = p;
+      }
+    }
+    if (cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) err = 1;
     return d;
   }
   void free_all() {
@@ -504,10 +592,25 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
   auto sysK = [&](int s) { return P.sys_K.empty() ? P.K : P.sys_K[s]; };
   const double t_begin = now_ms();
   double t_wait = 0;
+  PinnedStage stage;
+  struct StageGuard {
+    DevMem* m;
+    ~StageGuard() { m->stage = nullptr; }
+  } stage_guard{&F->mem};
+  F->mem.stage = &stage;
+  double t_mark = t_begin;
+  double ph_acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  auto mark = [&](int ph) {
+    const double t = now_ms();
+    ph_acc[ph] += t - t_mark;
+    t_mark = t;
+  };
+
   auto sync_st = [&]() -> cudaError_t {
     const double t0 = now_ms();
     const cudaError_t e = cudaStreamSynchronize(st);
     t_wait += now_ms() - t0;
+    if (e == cudaSuccess) stage.reset();    // every queued upload has been read
     return e;
   };
   F->N = (int)P.n_dof();
@@ -558,6 +661,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
 
   DevMem lvmem;  // memory of the current level arena (freed after compression)
   lvmem.st = st;
+  lvmem.stage = &stage;
   SPAND_TRY(layout(P.lv[0], n, lvmem));
   for (int q = 0; q < nsys; ++q) {
     // gather the BSR blocks of system q into the level-0 cluster blocks
@@ -565,6 +669,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
     const int Kq = sysK(q), Bq = sysB(q), e0 = sysE0(q);
     DevMem tmp;
     tmp.st = st;
+    tmp.stage = &stage;
     std::vector<int> rp(Kq + 1), col(A->nnzb);
     SPAND_CUDA_TRY(cudaMemcpyAsync(rp.data(), A->row_ptr, sizeof(int) * (Kq + 1), cudaMemcpyDeviceToHost, st));
     SPAND_CUDA_TRY(cudaMemcpyAsync(col.data(), A->col, sizeof(int) * A->nnzb, cudaMemcpyDeviceToHost, st));
@@ -663,10 +768,12 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
     }
     DevMem tmp;
     tmp.st = st;
+    tmp.stage = &stage;
     // neighbour lists in the current pattern
     std::vector<std::vector<int>> nbr(nc);
     for (auto& pr : L.pattern)
       if (pr.first != pr.second) nbr[pr.first].push_back(pr.second);
+    mark(0);
     // ================= 1. eliminate interiors (Eq. 9)
     std::vector<int> I;
     for (int c = 0; c < nc; ++c)
@@ -768,6 +875,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       tmp.free_all();
       break;
     }
+    mark(1);
     // ================= 2. scale interfaces (Eq. 10)
     std::vector<int> Fc;
     for (int c = 0; c < nc; ++c)
@@ -833,12 +941,27 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       launch_gemm(tmp, t1, m1, st);
       launch_gemm(tmp, t2, m2, st);
     }
+    mark(2);
     // ================= 3. all Q first (Eq. 11): RRQR of [A_sn A_ns^T]
     std::vector<QrTask<T>> qt;
     std::vector<int> qcl;
     std::vector<CopyTask<T>> cps;
     int* d_rank = tmp.alloc<int>(std::max<size_t>(Fc.size(), 1));
     int nmax_qr = 0;
+    // the reflector arrays of all interfaces in one zeroed allocation (zero
+    // above the diagonal for the WY products)
+    size_t vtot = 0;
+    for (size_t q = 0; q < Fc.size(); ++q) {
+      const int s = Fc[q];
+      if (nba[s].empty()) continue;
+      int cs = 0;
+      for (int b : nba[s]) cs += 2 * n[b];
+      vtot += (((size_t)n[s] * std::min(n[s], cs)) + 63) & ~size_t(63);
+    }
+    T* vall = tmp.alloc<T>(std::max<size_t>(vtot, 1));
+    if (tmp.err) return SPAND_ERR_NOMEM;
+    SPAND_CUDA_TRY(cudaMemsetAsync(vall, 0, sizeof(T) * std::max<size_t>(vtot, 1), st));
+    size_t voff = 0;
     for (size_t q = 0; q < Fc.size(); ++q) {
       const int s = Fc[q];
       if (nba[s].empty()) continue;
@@ -848,7 +971,8 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       t.n = n[s];
       t.c = cs;
       t.W = tmp.alloc<T>((size_t)n[s] * cs);             // row-major n x c
-      t.V = tmp.alloc<T>((size_t)n[s] * std::min(n[s], cs));
+      t.V = vall + voff;
+      voff += (((size_t)n[s] * std::min(n[s], cs)) + 63) & ~size_t(63);
       t.tau = tmp.alloc<T>(std::min(n[s], cs));
       t.norm2 = tmp.alloc<T>(cs);
       t.Q = nullptr;
@@ -873,8 +997,6 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
     std::vector<int> rank(qt.size());
     int qf[4] = {0, 0, 0, 0};
     if (!qt.empty()) {
-      // reflector storage must be zero above the diagonal for the WY products
-      for (auto& q : qt) SPAND_CUDA_TRY(cudaMemsetAsync(q.V, 0, sizeof(T) * (size_t)q.n * std::min(q.n, q.c), st));
       // 16-CTA clusters (non-portable size) where the device schedules them
       // (per device: an on-chip probe of the two 16-CTA kernels)
       static std::atomic<uint64_t> probed{0}, can16{0};
@@ -1095,9 +1217,11 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       S.rrqr_launches += 1;
       SPAND_CUDA_TRY(cudaMemcpyAsync(rank.data(), d_rank, sizeof(int) * qt.size(), cudaMemcpyDeviceToHost, st));
     }
+    mark(3);
     int hflags[4];
     SPAND_CUDA_TRY(cudaMemcpyAsync(hflags, d_flags, sizeof(hflags), cudaMemcpyDeviceToHost, st));
     SPAND_CUDA_TRY(sync_st());
+    mark(4);
     if (hflags[0] & 1) return SPAND_ERR_ZERO_PIVOT;   // the root cause when both are set
     if (hflags[0] & 2) return SPAND_ERR_NONFINITE;
     if (hflags[0] & 16) {
@@ -1204,6 +1328,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       }
       R.fa.push_back(f);
     }
+    mark(5);
     // ================= 4. next level: sizes, slots, merged blocks
     const LevelInfo& L2 = P.lv[l + 1];
     const int nc2 = (int)L2.cl.size();
@@ -1221,6 +1346,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
     // new arena
     DevMem lvmem2;
     lvmem2.st = st;
+    lvmem2.stage = &stage;
     T* old_arena = arena;
     std::map<std::pair<int, int>, size_t> old_off = boff;
     SPAND_TRY(layout(L2, n2, lvmem2));
@@ -1272,6 +1398,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
   }
   S.factor_flops = flops;
 
+  mark(6);
   // ================= apply program
   F->w = pm.alloc<T>(F->N);
   F->z = pm.alloc<T>(F->N);
@@ -1299,6 +1426,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
     if (!pt.empty()) {
       DevMem tmpp;
       tmpp.st = st;
+      tmpp.stage = &stage;
       auto* dpt = tmpp.upload(pt);
       if (tmpp.err) return SPAND_ERR_NOMEM;
       note_launch();
@@ -1524,8 +1652,10 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
     }
 
   S.factor_bytes = F->progs[0]->bytes;
+  mark(7);
   S.t_host_ms = now_ms() - t_begin;
   S.t_wait_ms = t_wait;
+  for (int i = 0; i < 8; ++i) S.t_host_phase_ms[i] = ph_acc[i];
   if (pm.err) return SPAND_ERR_NOMEM;
   SPAND_CUDA_TRY(cudaGetLastError());
   SPAND_CUDA_TRY(sync_st());
