@@ -27,6 +27,7 @@ struct MatRef {      // square matrix for getrf / inverses
   int n;
   int* ipiv;         // n pivots (absolute 0-based rows)
   int* perm;         // n: (P^T b)[k] = b[perm[k]]
+  int* aff;          // getrf scratch: per matrix of a batch, the rows a panel moves (1 + 4 LU_NB ints)
 };
 
 template <typename T>
@@ -210,11 +211,12 @@ __global__ void __launch_bounds__(256) k_getrf_panel(const MatRef<T>* mats, int 
   }
 }
 
-// Same contract as k_getrf_panel, with the panel (rows k0..n-1 of the 32 panel
+// The panel step of k_getrf_panel with the panel (rows k0..n-1 of the 32 panel
 // columns) staged in shared memory: pivot search, interchanges, scaling and the
-// rank-1 updates run on-chip; afterwards the panel is written back, its row
-// interchanges are applied to the columns outside the panel, and U12 =
-// L11^-1 A12 is formed.  Used when (n - k0) * 32 values fit the shared budget.
+// rank-1 updates run on-chip; afterwards the panel is written back and the rows
+// its interchanges move are recorded for k_getrf_swap_trsm, which updates the
+// columns outside the panel.  Used when (n - k0) * 32 values fit the shared
+// budget.
 constexpr int LU_SMEM_BYTES = 160 * 1024;
 
 template <typename T>
@@ -223,7 +225,6 @@ __global__ void __launch_bounds__(256) k_getrf_panel_smem(const MatRef<T>* mats,
   T* P = reinterpret_cast<T*>(lu_smem);          // panel, column-major m x jb (ld m)
   __shared__ T sv[32];
   __shared__ int si[32];
-  __shared__ T L11[LU_NB][LU_NB + 1];
   __shared__ int piv_loc[LU_NB];
   const int b = blockIdx.x;
   if (b >= nmat) return;
@@ -278,39 +279,96 @@ __global__ void __launch_bounds__(256) k_getrf_panel_smem(const MatRef<T>* mats,
     const int r = idx % m, c = idx / m;
     A[(k0 + r) + (size_t)(k0 + c) * ld] = P[idx];
   }
-  // row interchanges on the columns outside the panel: a thread per column
-  for (int c = threadIdx.x; c < n - jb; c += blockDim.x) {
-    const int col = (c < k0) ? c : c + jb;
-    T* colp = A + (size_t)col * ld + k0;
+  // the panel's interchanges as one row gather for the columns outside it:
+  // after the swaps, row pos[i] holds what row src[i] held (rows relative to
+  // k0; at most 2 jb rows move).  Applied by k_getrf_swap_trsm.
+  if (threadIdx.x == 0) {
+    int pos[2 * LU_NB], src[2 * LU_NB];
+    int cnt = 0;
     for (int j = 0; j < jb; ++j) {
-      const int p = piv_loc[j];
-      if (p != j) {
-        const T t = colp[j];
-        colp[j] = colp[p];
-        colp[p] = t;
+      pos[cnt] = j;
+      src[cnt] = j;
+      ++cnt;
+    }
+    for (int j = 0; j < jb; ++j) {
+      const int pj = piv_loc[j];
+      if (pj == j) continue;
+      int a = -1, b = -1;
+      for (int t = 0; t < cnt; ++t) {
+        if (pos[t] == j) a = t;
+        if (pos[t] == pj) b = t;
       }
+      if (b < 0) {                     // first time row pj moves
+        pos[cnt] = pj;
+        src[cnt] = pj;
+        b = cnt++;
+      }
+      const int t = src[a];
+      src[a] = src[b];
+      src[b] = t;
+    }
+    int* rec = M.aff + (size_t)b * (1 + 4 * LU_NB);
+    rec[0] = cnt;
+    for (int t = 0; t < cnt; ++t) {
+      rec[1 + t] = pos[t];
+      rec[1 + 2 * LU_NB + t] = src[t];
     }
   }
-  for (int t = threadIdx.x; t < jb * jb; t += blockDim.x) {
-    const int r = t % jb, c = t / jb;
-    L11[r][c] = P[r + c * m];
+}
+
+// The columns outside the panel of every matrix: apply the panel's row
+// interchanges (one gather of at most 2 jb rows per column) and, right of the
+// panel, form U12 = L11^-1 A12 by forward substitution.  A CTA handles 32
+// columns of one matrix, a warp one column at a time (lane r holds row k0+r).
+struct LuColTile {
+  int mat, c0;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_getrf_swap_trsm(const MatRef<T>* mats, const LuColTile* tiles, int k0) {
+  __shared__ T L11[LU_NB][LU_NB + 1];
+  __shared__ int s_pos[2 * LU_NB], s_src[2 * LU_NB];
+  __shared__ int s_cnt;
+  const LuColTile tl = tiles[blockIdx.x];
+  const MatRef<T> M = mats[tl.mat];
+  const int n = M.n;
+  const size_t ld = n;
+  const int jb = min(LU_NB, n - k0);
+  const int* rec = M.aff + (size_t)tl.mat * (1 + 4 * LU_NB);
+  if (threadIdx.x == 0) s_cnt = rec[0];
+  for (int t = threadIdx.x; t < 2 * LU_NB; t += blockDim.x) {
+    s_pos[t] = rec[1 + t];
+    s_src[t] = rec[1 + 2 * LU_NB + t];
+  }
+  for (int t = threadIdx.x; t < LU_NB * LU_NB; t += blockDim.x) {
+    const int r = t % LU_NB, c = t / LU_NB;
+    L11[r][c] = (r < jb && c < jb) ? M.A[(k0 + r) + (size_t)(k0 + c) * ld] : (T)0;
   }
   __syncthreads();
-  for (int c = k0 + jb + threadIdx.x; c < n; c += blockDim.x) {
-    T x[LU_NB];
-    T* col = A + (size_t)c * ld + k0;
-#pragma unroll
-    for (int r = 0; r < LU_NB; ++r) x[r] = (r < jb) ? col[r] : (T)0;
-#pragma unroll
-    for (int r = 1; r < LU_NB; ++r) {
-      T s = x[r];
-#pragma unroll
-      for (int q = 0; q < r; ++q) s -= L11[r][q] * x[q];
-      x[r] = s;
+  const int cnt = s_cnt;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int cc = wid; cc < 32; cc += 8) {
+    const int c = tl.c0 + cc;                       // column index among the n - jb outside ones
+    if (c >= n - jb) break;
+    const int col = (c < k0) ? c : c + jb;
+    T* colp = M.A + (size_t)col * ld + k0;
+    // gather the moved rows: read all sources first, then write
+    T v0 = 0, v1 = 0;
+    if (lane < cnt) v0 = colp[s_src[lane]];
+    if (lane + 32 < cnt) v1 = colp[s_src[lane + 32]];
+    __syncwarp();
+    if (lane < cnt) colp[s_pos[lane]] = v0;
+    if (lane + 32 < cnt) colp[s_pos[lane + 32]] = v1;
+    __syncwarp();
+    if (col >= k0 + jb) {
+      // U12 column: x = L11^-1 x over rows k0 .. k0+jb-1
+      T x = (lane < jb) ? colp[lane] : (T)0;
+      for (int q = 0; q < jb - 1; ++q) {
+        const T xq = __shfl_sync(0xffffffffu, x, q);
+        if (lane > q) x -= L11[lane][q] * xq;
+      }
+      if (lane < jb) colp[lane] = x;
     }
-#pragma unroll
-    for (int r = 0; r < LU_NB; ++r)
-      if (r < jb) col[r] = x[r];
   }
 }
 
@@ -1014,9 +1072,11 @@ constexpr int QR_THREADS = 512;
 template <typename T, int CS>
 struct ClusterX {
   static constexpr int kMax = CS;
+  static constexpr bool kOneSync = true;  // every CTA reads the pivot column itself
   cooperative_groups::cluster_group cl;
-  T* cand_v;
+  T* cand_v;                              // [2]: proposals double-buffered by step parity
   int* cand_i;
+  int par = 0;
   __device__ int rank() const { return (int)cl.block_rank(); }
   __device__ int size() const { return CS; }
   __device__ bool sync() {
@@ -1024,13 +1084,16 @@ struct ClusterX {
     return true;
   }
   __device__ void publish(T v, int i) {   // thread 0
-    *cand_v = v;
-    *cand_i = i;
+    cand_v[par] = v;
+    cand_i[par] = i;
   }
   __device__ void gather(int r, T& v, int& i) {
-    v = *cl.map_shared_rank(cand_v, r);
-    i = *cl.map_shared_rank(cand_i, r);
+    v = *cl.map_shared_rank(cand_v + par, r);
+    i = *cl.map_shared_rank(cand_i + par, r);
   }
+  __device__ void next_step() { par ^= 1; }
+  template <typename U>
+  __device__ U* remote(U* p, int r) { return cl.map_shared_rank(p, r); }
   // copy rows k..n-1 of the owner's reflector and its tau into this CTA
   __device__ void fetch_reflector(T* v, T* s_tau, const QrTask<T>&, int k, int n, int owner, int tid, int nt) {
     const T* rv = cl.map_shared_rank(v, owner);
@@ -1049,6 +1112,7 @@ constexpr int QR_GMAX = 256;     // largest CTA group of the cooperative variant
 template <typename T>
 struct GroupX {
   static constexpr int kMax = QR_GMAX;
+  static constexpr bool kOneSync = false;
   int q, G;
   T* prop_v;                 // G proposals of this group (global)
   int* prop_i;
@@ -1092,6 +1156,9 @@ struct GroupX {
     v = __ldcg(prop_v + r);
     i = __ldcg(prop_i + r);
   }
+  __device__ void next_step() {}
+  template <typename U>
+  __device__ U* remote(U* p, int) { return p; }
   __device__ void fetch_reflector(T* v, T* s_tau, const QrTask<T>& tk, int k, int n, int, int tid, int nt) {
     const T* col = tk.V + (size_t)k * n;
     for (int i = k + tid; i < n; i += nt) v[i] = __ldcg(col + i);
@@ -1217,37 +1284,75 @@ __device__ void qrcp_group(const QrTask<T>& tk, T eps, X& xc, unsigned char* sme
     }
     const int p = gi;
     const bool owner = (p >= j0 && p < j1);
-    if (owner) {
-      // Householder vector of column p, rows k..n-1
-      T prt = 0;
-      for (int i = k + 1 + tid; i < n; i += NT) {
-        const T a = at(i, p);
-        prt += a * a;
+    const int orank = p / chunk;
+    if constexpr (X::kOneSync) {
+      // every CTA builds the same reflector from column p, read from the owner
+      // (its shared memory through the cluster, or W in global memory); the
+      // owner never touches a used column again, so no second barrier is needed
+      if (SMEM) {
+        const T* ws_o = xc.remote(Ws, orank);
+        const int pj = p - orank * chunk;
+        for (int i = k + tid; i < n; i += NT) v[i] = ws_o[(size_t)i * chunk + pj];
+      } else {
+        for (int i = k + tid; i < n; i += NT) v[i] = owner ? at(i, p) : __ldcg(Wg + (size_t)i * ldg + p);
       }
+      __syncthreads();
+      T prt = 0;
+      for (int i = k + 1 + tid; i < n; i += NT) prt += v[i] * v[i];
       const T sigma = block_sum(prt, red_v);
-      const T alpha = at(k, p);
+      const T alpha = v[k];
       T tau = 2, beta = -alpha, scale = 0;          // column already reduced: H = I - 2 e_k e_k^T
       if (sigma > (T)0) {
         beta = -copysign(sqrt(alpha * alpha + sigma), alpha);
         tau = (beta - alpha) / beta;
         scale = (T)1 / (alpha - beta);
       }
+      __syncthreads();
       for (int i = k + tid; i < n; i += NT) {
-        const T vi = (i == k) ? (T)1 : at(i, p) * scale;
+        const T vi = (i == k) ? (T)1 : v[i] * scale;
         v[i] = vi;
-        tk.V[(size_t)i + (size_t)k * n] = vi;
+        if (owner) tk.V[(size_t)i + (size_t)k * n] = vi;
       }
       if (tid == 0) {
         s_scal[0] = tau;
-        tk.tau[k] = tau;
-        tk.norm2[p] = -1;                  // used
+        if (owner) {
+          tk.tau[k] = tau;
+          tk.norm2[p] = -1;                // used
+        }
       }
+      __syncthreads();
+    } else {
+      if (owner) {
+        // Householder vector of column p, rows k..n-1
+        T prt = 0;
+        for (int i = k + 1 + tid; i < n; i += NT) {
+          const T a = at(i, p);
+          prt += a * a;
+        }
+        const T sigma = block_sum(prt, red_v);
+        const T alpha = at(k, p);
+        T tau = 2, beta = -alpha, scale = 0;        // column already reduced: H = I - 2 e_k e_k^T
+        if (sigma > (T)0) {
+          beta = -copysign(sqrt(alpha * alpha + sigma), alpha);
+          tau = (beta - alpha) / beta;
+          scale = (T)1 / (alpha - beta);
+        }
+        for (int i = k + tid; i < n; i += NT) {
+          const T vi = (i == k) ? (T)1 : at(i, p) * scale;
+          v[i] = vi;
+          tk.V[(size_t)i + (size_t)k * n] = vi;
+        }
+        if (tid == 0) {
+          s_scal[0] = tau;
+          tk.tau[k] = tau;
+          tk.norm2[p] = -1;                // used
+        }
+      }
+      if (!(ok = xc.sync())) break;
+      // ---- copy the reflector from the owner
+      if (!owner) xc.fetch_reflector(v, &s_scal[0], tk, k, n, orank, tid, NT);
+      __syncthreads();
     }
-    if (!(ok = xc.sync())) break;
-    // ---- copy the reflector from the owner
-    const int orank = p / chunk;
-    if (!owner) xc.fetch_reflector(v, &s_scal[0], tk, k, n, orank, tid, NT);
-    __syncthreads();
     const T tau = s_scal[0];
     // ---- update the own remaining columns and their norms; track the best
     T best = -1;
@@ -1301,6 +1406,7 @@ __device__ void qrcp_group(const QrTask<T>& tk, T eps, X& xc, unsigned char* sme
       s_prop_v = b2;
       s_prop_i = i2;
     }
+    xc.next_step();
   }
   if (q == 0 && tid == 0) *tk.rank = ok ? rank : 0;
   if (ok) xc.finish();
@@ -1309,11 +1415,11 @@ __device__ void qrcp_group(const QrTask<T>& tk, T eps, X& xc, unsigned char* sme
 template <typename T, bool SMEM, int CS, int NT>
 __global__ void __launch_bounds__(NT, 1) k_qrcp_cluster(const QrTask<T>* tasks, T eps) {
   extern __shared__ unsigned char qr_smem2[];
-  __shared__ T cand_v;
-  __shared__ int cand_i;
-  ClusterX<T, CS> xc{cooperative_groups::this_cluster(), &cand_v, &cand_i};
+  __shared__ T cand_v[2];
+  __shared__ int cand_i[2];
+  ClusterX<T, CS> xc{cooperative_groups::this_cluster(), cand_v, cand_i};
   const QrTask<T> tk = tasks[blockIdx.x / CS];
-  qrcp_group<T, SMEM, NT>(tk, eps, xc, qr_smem2, &cand_v, &cand_i, nullptr);
+  qrcp_group<T, SMEM, NT>(tk, eps, xc, qr_smem2, cand_v, cand_i, nullptr);
 }
 
 // Interfaces too large for one cluster: a cooperative launch in which group t

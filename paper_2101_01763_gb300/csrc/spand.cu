@@ -27,6 +27,7 @@
 
 #include "dense.cuh"
 #include "gemv.cuh"
+#include "umma.cuh"
 #include "internal.h"
 
 namespace spand {
@@ -226,14 +227,26 @@ static void upload3(DevMem& m, const std::vector<A>& a, const std::vector<B>& b,
 }
 
 // ------------------------------------------------------------------ launch helpers
+// FP32 products on the tcgen05 tensor cores unless SPAND_GEMM=mma selects the
+// mma.sync kernel (kept for comparison); the choice is read once per process
+static bool use_umma() {
+  static const bool on = [] {
+    const char* v = std::getenv("SPAND_GEMM");
+    return !(v && std::strcmp(v, "mma") == 0);
+  }();
+  return on;
+}
+
 template <typename T>
 static void launch_gemm(DevMem& tmp, const std::vector<GemmTask<T>>& tasks, const std::vector<GemmTerm<T>>& terms,
                         cudaStream_t st) {
+  const bool umma = std::is_same<T, float>::value && use_umma();
+  const int BM = umma ? UM_BM : 64, BN = umma ? UM_BN : 64;
   std::vector<TileItem> tiles;
   for (int t = 0; t < (int)tasks.size(); ++t) {
     if (tasks[t].m <= 0 || tasks[t].n <= 0) continue;
-    for (int a = 0; a < (tasks[t].m + 63) / 64; ++a)
-      for (int b = 0; b < (tasks[t].n + 63) / 64; ++b) tiles.push_back({t, a, b});
+    for (int a = 0; a < (tasks[t].m + BM - 1) / BM; ++a)
+      for (int b = 0; b < (tasks[t].n + BN - 1) / BN; ++b) tiles.push_back({t, a, b});
   }
   if (tiles.empty()) return;
   GemmTask<T>* dt;
@@ -242,10 +255,17 @@ static void launch_gemm(DevMem& tmp, const std::vector<GemmTask<T>>& tasks, cons
   upload3(tmp, tasks, terms, tiles, dt, dm, dl);
   if (tmp.err) return;
   note_launch();
-  if constexpr (std::is_same<T, float>::value)
-    k_gemm_tc<3><<<(unsigned)tiles.size(), 128, 0, st>>>(dt, dm, dl);   // FP32 factors: 3xTF32 tensor cores
-  else
+  if constexpr (std::is_same<T, float>::value) {
+    if (umma) {
+      static std::atomic<uint64_t> attr{0};
+      once_per_device(attr, [] { set_dyn_smem((const void*)k_gemm_umma, UM_SMEM_BYTES); });
+      k_gemm_umma<<<(unsigned)tiles.size(), 128, UM_SMEM_BYTES, st>>>(dt, dm, dl);
+    } else {
+      k_gemm_tc<3><<<(unsigned)tiles.size(), 128, 0, st>>>(dt, dm, dl);   // 3xTF32 on mma.sync
+    }
+  } else {
     k_gemm<T><<<(unsigned)tiles.size(), 256, 0, st>>>(dt, dm, dl);
+  }
 }
 
 template <typename T>
@@ -314,6 +334,10 @@ static void batched_getrf(DevMem& tmp, std::vector<MatRef<T>>& mats, int* d_flag
       large.push_back(m);
     }
   }
+  if (!small.empty()) {
+    int* aff = tmp.alloc<int>(small.size() * (1 + 4 * LU_NB));
+    for (auto& m : small) m.aff = aff;
+  }
   auto* ds = small.empty() ? nullptr : tmp.upload(small);
   auto* dlg = large.empty() ? nullptr : tmp.upload(large);
   if (tmp.err) return;
@@ -327,6 +351,20 @@ static void batched_getrf(DevMem& tmp, std::vector<MatRef<T>>& mats, int* d_flag
       const size_t sm = (size_t)(nsmall_max - k0) * std::min(LU_NB, nsmall_max - k0) * sizeof(T);
       note_launch();
       k_getrf_panel_smem<T><<<(unsigned)small.size(), 256, sm, st>>>(ds, (int)small.size(), k0, d_flags);
+      // the panel's interchanges and U12 on the columns outside it, 32 columns per CTA
+      std::vector<LuColTile> tl;
+      for (int b = 0; b < (int)small.size(); ++b) {
+        const int nb = small[b].n;
+        if (k0 >= nb) continue;
+        const int outside = nb - std::min(LU_NB, nb - k0);
+        for (int c0 = 0; c0 < outside; c0 += 32) tl.push_back({b, c0});
+      }
+      if (!tl.empty()) {
+        auto* dtl = tmp.upload(tl);
+        if (tmp.err) return;
+        note_launch();
+        k_getrf_swap_trsm<T><<<(unsigned)tl.size(), 256, 0, st>>>(ds, dtl, k0);
+      }
     }
     if (dlg) {
       note_launch();
@@ -1395,6 +1433,14 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
     S.t_elim_gemm_ms += ev_read(ev_gm[D]);
     if (hflags[0] & 1) return SPAND_ERR_ZERO_PIVOT;   // the root cause when both are set
     if (hflags[0] & 2) return SPAND_ERR_NONFINITE;
+    if (std::is_same<T, float>::value && use_umma()) {
+      int uf = 0;
+      SPAND_CUDA_TRY(cudaMemcpyFromSymbol(&uf, g_umma_fail, sizeof(int)));
+      if (uf) {
+        report_cuda_error(cudaErrorLaunchTimeout, "tcgen05 GEMM completion wait", __FILE__, __LINE__);
+        return SPAND_ERR_CUDA;
+      }
+    }
   }
   S.factor_flops = flops;
 

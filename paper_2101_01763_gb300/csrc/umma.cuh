@@ -1,0 +1,261 @@
+// Grouped FP32 GEMM on the 5th-generation tensor cores (tcgen05, sm_100 family).
+//
+// Same task / term / tile contract as k_gemm_tc (C = alpha * sum_t op(A_t) op(B_t)
+// + beta * C, column-major), on 128 x 64 output tiles:
+//  * 128 threads stage one 32-wide k-chunk of op(A) (128 x 32) and op(B)^T
+//    (64 x 32) in shared memory, split into TF32 high parts and TF32
+//    remainders, in the K-major "core matrix" layout the MMA reads without
+//    swizzling (8 rows x 16 bytes per core matrix);
+//  * one thread issues tcgen05.mma.kind::tf32 with the accumulator in tensor
+//    memory (128 lanes x 64 FP32 columns): hi*lo + lo*hi + hi*hi per 8-wide
+//    k-step (error-compensated 3xTF32, about FP32 accuracy), and commits the
+//    chunk to an mbarrier of its stage; two stages alternate so the staging
+//    of chunk i+1 overlaps the MMAs of chunk i;
+//  * the epilogue reads the accumulator with tcgen05.ld (warp w owns lanes
+//    32w..32w+31 = rows of the tile) and applies alpha / beta.
+// Every mbarrier wait is bounded; on timeout the CTA sets g_umma_fail (read by
+// the host after the factorization), skips its epilogue and frees its tensor
+// memory.
+#pragma once
+#include <cstdint>
+
+#include "dense.cuh"
+
+namespace spand {
+
+constexpr int UM_BM = 128, UM_BN = 64, UM_BK = 32;
+constexpr int UM_TMEM_COLS = 64;
+// bytes of one operand stage: A hi, A lo (128 x 32 x 4), B hi, B lo (64 x 32 x 4)
+constexpr int UM_A_BYTES = UM_BM * UM_BK * 4, UM_B_BYTES = UM_BN * UM_BK * 4;
+constexpr int UM_STAGE_BYTES = 2 * UM_A_BYTES + 2 * UM_B_BYTES;
+constexpr int UM_SMEM_BYTES = 2 * UM_STAGE_BYTES + 1024;   // two stages + alignment slack
+
+__device__ inline uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: K-major, no swizzle; lbo = byte step between
+// core matrices along K, sbo = byte step between 8-row groups
+__device__ inline uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;                       // descriptor version of the sm_100 family
+  return d;                                     // base offset 0, relative LBO, no swizzle
+}
+
+// instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = 64
+__host__ __device__ constexpr uint32_t umma_idesc_tf32() {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(UM_BN >> 3) << 17) | ((uint32_t)(UM_BM >> 4) << 24);
+}
+
+// byte offset of element (r, k) of a K-major operand of 32-wide k-chunks:
+// core matrix (r/8, k/4) of 8 rows x 4 elements; k-neighbour core matrices
+// 128 bytes apart, 8-row groups 1024 bytes apart
+__device__ inline uint32_t umma_off(int r, int k) {
+  return (uint32_t)((r >> 3) * 1024 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4);
+}
+
+__device__ inline bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (long it = 0; it < (1l << 24); ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ int g_umma_fail;   // set when an MMA completion wait ran out of time
+
+__global__ void __launch_bounds__(128, 1) k_gemm_umma(const GemmTask<float>* tasks, const GemmTerm<float>* terms,
+                                                      const TileItem* tiles) {
+  extern __shared__ unsigned char um_raw[];
+  __shared__ uint64_t mbar[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
+  // 1024-byte aligned operand area
+  unsigned char* um = um_raw + ((1024 - (smem_u32(um_raw) & 1023)) & 1023);
+  const TileItem it = tiles[blockIdx.x];
+  const GemmTask<float> tk = tasks[it.task];
+  const int i0 = it.tm * UM_BM, j0 = it.tn * UM_BN;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(UM_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    s_fail = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+
+  // flattened (term, k-chunk) sequence, as in k_gemm_tc
+  int cur_t = tk.t0, cur_l = 0;
+  while (cur_t < tk.t1 && term_klim(terms[cur_t], i0, j0, UM_BM, UM_BN) <= 0) ++cur_t;
+  int item = 0;
+  bool failed = false;
+  while (cur_t < tk.t1) {
+    const int s = item & 1;
+    unsigned char* st = um + s * UM_STAGE_BYTES;
+    if (item >= 2) {
+      // the MMAs that read this stage two chunks ago must be done (the outcome
+      // is made uniform over the CTA so every thread leaves the loop together)
+      const bool ok = mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((item >> 1) - 1) & 1));
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+    }
+    // ---- stage op(A) rows i0..i0+127 and op(B) columns j0..j0+63 of k-chunk cur_l
+    const GemmTerm<float> tm = terms[cur_t];
+    {
+      // A: thread = row; 32 k values, split into hi / lo
+      const int r = tid, gi = i0 + r;
+#pragma unroll 4
+      for (int kq = 0; kq < UM_BK; kq += 4) {
+        float x[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int gl = cur_l + kq + e;
+          x[e] = (gi < tk.m && gl < tm.k)
+                     ? (tm.ta ? tm.A[gl + (size_t)gi * tm.lda] : tm.A[gi + (size_t)gl * tm.lda])
+                     : 0.f;
+        }
+        uint4 hi, lo;
+        hi.x = to_tf32(x[0]);
+        hi.y = to_tf32(x[1]);
+        hi.z = to_tf32(x[2]);
+        hi.w = to_tf32(x[3]);
+        lo.x = to_tf32(x[0] - __uint_as_float(hi.x));
+        lo.y = to_tf32(x[1] - __uint_as_float(hi.y));
+        lo.z = to_tf32(x[2] - __uint_as_float(hi.z));
+        lo.w = to_tf32(x[3] - __uint_as_float(hi.w));
+        const uint32_t off = umma_off(r, kq);
+        *reinterpret_cast<uint4*>(st + off) = hi;
+        *reinterpret_cast<uint4*>(st + UM_A_BYTES + off) = lo;
+      }
+      // B^T: threads 0..63 = columns, 32 k values each; threads 64..127 split the k range
+      const int c = tid & 63, half = tid >> 6, gj = j0 + c;
+#pragma unroll 2
+      for (int kq = half * 16; kq < half * 16 + 16; kq += 4) {
+        float y[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int gl = cur_l + kq + e;
+          y[e] = (gj < tk.n && gl < tm.k)
+                     ? (tm.tb ? tm.B[gj + (size_t)gl * tm.ldb] : tm.B[gl + (size_t)gj * tm.ldb])
+                     : 0.f;
+        }
+        uint4 hi, lo;
+        hi.x = to_tf32(y[0]);
+        hi.y = to_tf32(y[1]);
+        hi.z = to_tf32(y[2]);
+        hi.w = to_tf32(y[3]);
+        lo.x = to_tf32(y[0] - __uint_as_float(hi.x));
+        lo.y = to_tf32(y[1] - __uint_as_float(hi.y));
+        lo.z = to_tf32(y[2] - __uint_as_float(hi.z));
+        lo.w = to_tf32(y[3] - __uint_as_float(hi.w));
+        const uint32_t off = umma_off(c, kq);
+        *reinterpret_cast<uint4*>(st + 2 * UM_A_BYTES + off) = hi;
+        *reinterpret_cast<uint4*>(st + 2 * UM_A_BYTES + UM_B_BYTES + off) = lo;
+      }
+    }
+    // the generic-proxy stores must be visible to the tensor core (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t a_hi = smem_u32(st), a_lo = a_hi + UM_A_BYTES;
+      const uint32_t b_hi = a_hi + 2 * UM_A_BYTES, b_lo = b_hi + UM_B_BYTES;
+      const uint32_t idesc = umma_idesc_tf32();
+#pragma unroll
+      for (int ks = 0; ks < UM_BK / 8; ++ks) {
+        const uint32_t ko = ks * 256;            // two core matrices along K per 8-wide step
+        const uint64_t dah = umma_desc(a_hi + ko, 128, 1024), dal = umma_desc(a_lo + ko, 128, 1024);
+        const uint64_t dbh = umma_desc(b_hi + ko, 128, 1024), dbl = umma_desc(b_lo + ko, 128, 1024);
+        const uint32_t acc0 = (item > 0 || ks > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                tmem),
+            "l"(dal), "l"(dbh), "r"(idesc), "r"(acc0));
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                tmem),
+            "l"(dah), "l"(dbl), "r"(idesc), "r"(1u));
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                tmem),
+            "l"(dah), "l"(dbh), "r"(idesc), "r"(1u));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&mbar[s])));
+    }
+    ++item;
+    cur_l += UM_BK;
+    while (cur_t < tk.t1 && cur_l >= term_klim(terms[cur_t], i0, j0, UM_BM, UM_BN)) {
+      ++cur_t;
+      cur_l = 0;
+    }
+  }
+  // ---- wait for the last committed chunk (it tracks every earlier MMA of the thread)
+  if (item > 0 && !failed) {
+    const int last = item - 1;
+    if (!mbar_wait(smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1))) failed = true;
+  }
+  if (failed) atomicOr(&s_fail, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (s_fail) {
+    if (tid == 0) atomicOr(&g_umma_fail, 1);
+  } else {
+    // ---- epilogue: warp w holds rows 32w..32w+31 of the tile, 64 columns each
+    const int row = warp * 32 + lane, gi = i0 + row;
+#pragma unroll
+    for (int cb = 0; cb < UM_BN; cb += 16) {
+      uint32_t v[16];
+      if (item > 0) {
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      } else {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) v[e] = 0u;
+      }
+      if (gi < tk.m) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int gj = j0 + cb + e;
+          if (gj < tk.n) {
+            float* cp = tk.C + gi + (size_t)gj * tk.ldc;
+            float val = tk.alpha * __uint_as_float(v[e]);
+            if (tk.beta != 0.f) val += tk.beta * *cp;
+            *cp = val;
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(UM_TMEM_COLS));
+  }
+}
+
+}  // namespace spand
