@@ -240,7 +240,20 @@ static bool use_umma() {
 template <typename T>
 static void launch_gemm(DevMem& tmp, const std::vector<GemmTask<T>>& tasks, const std::vector<GemmTerm<T>>& terms,
                         cudaStream_t st) {
-  const bool umma = std::is_same<T, float>::value && use_umma();
+  // tcgen05 pays off when a tile runs several 32-wide k-chunks (its set-up --
+  // tensor-memory allocation, barriers, the accumulator read-back -- is then
+  // amortised); short-k products (LU trailing updates) stay on mma.sync
+  bool umma = std::is_same<T, float>::value && use_umma();
+  if (umma) {
+    double chunks = 0;
+    int ntask = 0;
+    for (const auto& tk : tasks) {
+      if (tk.m <= 0 || tk.n <= 0) continue;
+      for (int t = tk.t0; t < tk.t1; ++t) chunks += (terms[t].k + UM_BK - 1) / UM_BK;
+      ++ntask;
+    }
+    umma = ntask > 0 && chunks >= 4.0 * ntask;
+  }
   const int BM = umma ? UM_BM : 64, BN = umma ? UM_BN : 64;
   std::vector<TileItem> tiles;
   for (int t = 0; t < (int)tasks.size(); ++t) {

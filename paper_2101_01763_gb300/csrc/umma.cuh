@@ -70,7 +70,7 @@ __device__ inline bool mbar_wait(uint32_t bar, uint32_t parity) {
 
 __device__ int g_umma_fail;   // set when an MMA completion wait ran out of time
 
-__global__ void __launch_bounds__(128, 1) k_gemm_umma(const GemmTask<float>* tasks, const GemmTerm<float>* terms,
+__global__ void __launch_bounds__(128, 2) k_gemm_umma(const GemmTask<float>* tasks, const GemmTerm<float>* terms,
                                                       const TileItem* tiles) {
   extern __shared__ unsigned char um_raw[];
   __shared__ uint64_t mbar[2];
@@ -119,53 +119,81 @@ __global__ void __launch_bounds__(128, 1) k_gemm_umma(const GemmTask<float>* tas
     // ---- stage op(A) rows i0..i0+127 and op(B) columns j0..j0+63 of k-chunk cur_l
     const GemmTerm<float> tm = terms[cur_t];
     {
-      // A: thread = row; 32 k values, split into hi / lo
+      // all global loads of the chunk are issued before any conversion, as
+      // 16-byte loads where k is the contiguous direction and alignment allows
+      // A: thread = row, 32 k values
       const int r = tid, gi = i0 + r;
-#pragma unroll 4
-      for (int kq = 0; kq < UM_BK; kq += 4) {
-        float x[4];
+      float x[UM_BK];
+      const bool a_vec = tm.ta && ((tm.lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(tm.A) & 15) == 0) &&
+                         cur_l + UM_BK <= tm.k;
+      if (a_vec && gi < tk.m) {
+        const float4* src = reinterpret_cast<const float4*>(tm.A + cur_l + (size_t)gi * tm.lda);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int gl = cur_l + kq + e;
-          x[e] = (gi < tk.m && gl < tm.k)
-                     ? (tm.ta ? tm.A[gl + (size_t)gi * tm.lda] : tm.A[gi + (size_t)gl * tm.lda])
-                     : 0.f;
+        for (int q = 0; q < UM_BK / 4; ++q) {
+          const float4 f = src[q];
+          x[4 * q] = f.x;
+          x[4 * q + 1] = f.y;
+          x[4 * q + 2] = f.z;
+          x[4 * q + 3] = f.w;
         }
+      } else {
+#pragma unroll
+        for (int e = 0; e < UM_BK; ++e) {
+          const int gl = cur_l + e;
+          x[e] = (gi < tk.m && gl < tm.k) ? (tm.ta ? tm.A[gl + (size_t)gi * tm.lda] : tm.A[gi + (size_t)gl * tm.lda])
+                                          : 0.f;
+        }
+      }
+      // B^T: threads 0..63 = columns (k 0..15), threads 64..127 the same columns (k 16..31)
+      const int c = tid & 63, half = tid >> 6, gj = j0 + c, kb = cur_l + half * 16;
+      float y[16];
+      const bool b_vec = !tm.tb && ((tm.ldb & 3) == 0) && ((reinterpret_cast<uintptr_t>(tm.B) & 15) == 0) &&
+                         kb + 16 <= tm.k;
+      if (b_vec && gj < tk.n) {
+        const float4* src = reinterpret_cast<const float4*>(tm.B + kb + (size_t)gj * tm.ldb);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 f = src[q];
+          y[4 * q] = f.x;
+          y[4 * q + 1] = f.y;
+          y[4 * q + 2] = f.z;
+          y[4 * q + 3] = f.w;
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int gl = kb + e;
+          y[e] = (gj < tk.n && gl < tm.k) ? (tm.tb ? tm.B[gj + (size_t)gl * tm.ldb] : tm.B[gl + (size_t)gj * tm.ldb])
+                                          : 0.f;
+        }
+      }
+#pragma unroll
+      for (int kq = 0; kq < UM_BK; kq += 4) {
         uint4 hi, lo;
-        hi.x = to_tf32(x[0]);
-        hi.y = to_tf32(x[1]);
-        hi.z = to_tf32(x[2]);
-        hi.w = to_tf32(x[3]);
-        lo.x = to_tf32(x[0] - __uint_as_float(hi.x));
-        lo.y = to_tf32(x[1] - __uint_as_float(hi.y));
-        lo.z = to_tf32(x[2] - __uint_as_float(hi.z));
-        lo.w = to_tf32(x[3] - __uint_as_float(hi.w));
+        hi.x = to_tf32(x[kq]);
+        hi.y = to_tf32(x[kq + 1]);
+        hi.z = to_tf32(x[kq + 2]);
+        hi.w = to_tf32(x[kq + 3]);
+        lo.x = to_tf32(x[kq] - __uint_as_float(hi.x));
+        lo.y = to_tf32(x[kq + 1] - __uint_as_float(hi.y));
+        lo.z = to_tf32(x[kq + 2] - __uint_as_float(hi.z));
+        lo.w = to_tf32(x[kq + 3] - __uint_as_float(hi.w));
         const uint32_t off = umma_off(r, kq);
         *reinterpret_cast<uint4*>(st + off) = hi;
         *reinterpret_cast<uint4*>(st + UM_A_BYTES + off) = lo;
       }
-      // B^T: threads 0..63 = columns, 32 k values each; threads 64..127 split the k range
-      const int c = tid & 63, half = tid >> 6, gj = j0 + c;
-#pragma unroll 2
-      for (int kq = half * 16; kq < half * 16 + 16; kq += 4) {
-        float y[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int gl = cur_l + kq + e;
-          y[e] = (gj < tk.n && gl < tm.k)
-                     ? (tm.tb ? tm.B[gj + (size_t)gl * tm.ldb] : tm.B[gl + (size_t)gj * tm.ldb])
-                     : 0.f;
-        }
+      for (int kq = 0; kq < 16; kq += 4) {
         uint4 hi, lo;
-        hi.x = to_tf32(y[0]);
-        hi.y = to_tf32(y[1]);
-        hi.z = to_tf32(y[2]);
-        hi.w = to_tf32(y[3]);
-        lo.x = to_tf32(y[0] - __uint_as_float(hi.x));
-        lo.y = to_tf32(y[1] - __uint_as_float(hi.y));
-        lo.z = to_tf32(y[2] - __uint_as_float(hi.z));
-        lo.w = to_tf32(y[3] - __uint_as_float(hi.w));
-        const uint32_t off = umma_off(c, kq);
+        hi.x = to_tf32(y[kq]);
+        hi.y = to_tf32(y[kq + 1]);
+        hi.z = to_tf32(y[kq + 2]);
+        hi.w = to_tf32(y[kq + 3]);
+        lo.x = to_tf32(y[kq] - __uint_as_float(hi.x));
+        lo.y = to_tf32(y[kq + 1] - __uint_as_float(hi.y));
+        lo.z = to_tf32(y[kq + 2] - __uint_as_float(hi.z));
+        lo.w = to_tf32(y[kq + 3] - __uint_as_float(hi.w));
+        const uint32_t off = umma_off(c, half * 16 + kq);
         *reinterpret_cast<uint4*>(st + 2 * UM_A_BYTES + off) = hi;
         *reinterpret_cast<uint4*>(st + 2 * UM_A_BYTES + UM_B_BYTES + off) = lo;
       }
