@@ -19,6 +19,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <memory>
 #include <new>
@@ -227,32 +228,122 @@ static void upload3(DevMem& m, const std::vector<A>& a, const std::vector<B>& b,
 }
 
 // ------------------------------------------------------------------ launch helpers
-// FP32 products on the tcgen05 tensor cores unless SPAND_GEMM=mma selects the
-// mma.sync kernel (kept for comparison); the choice is read once per process
-static bool use_umma() {
-  static const bool on = [] {
+// FP32 products: the tcgen05 kernel (128 x 64 tiles, tensor-memory accumulator)
+// or the mma.sync kernel (64 x 64 tiles).  SPAND_GEMM=umma / mma forces one;
+// by default an online tuner picks per class of launch (below).
+static int gemm_mode() {   // 0: tuned, 1: tcgen05, 2: mma.sync
+  static const int m = [] {
     const char* v = std::getenv("SPAND_GEMM");
-    return !(v && std::strcmp(v, "mma") == 0);
+    if (v && std::strcmp(v, "mma") == 0) return 2;
+    if (v && std::strcmp(v, "umma") == 0) return 1;
+    return 0;
   }();
-  return on;
+  return m;
+}
+
+// Online tuner for the choice of GEMM kernel (and with it the tile shape).
+// Launches are grouped by device, the average number of 32-wide k-chunks per
+// product (log2 bucket) and the logical flop count (log2 bucket).  The first
+// launches of a class run each candidate once between two events; once both
+// timings have completed (checked without waiting, at a later launch of the
+// class) the candidate with the lower time per flop is used for the class for
+// the rest of the process.  Until then -- and whenever a measurement is still
+// in flight -- the rule "tcgen05 from four k-chunks per product on" decides.
+// Either kernel computes the same products; only FP32 rounding order differs.
+struct GemmTuner {
+  struct Entry {
+    int choice = -1;                 // decided: 0 tcgen05, 1 mma.sync
+    bool pending[2] = {false, false};
+    bool done[2] = {false, false};
+    double per_flop[2] = {0, 0};
+    double flops[2] = {0, 0};
+    cudaEvent_t ev[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  };
+  std::mutex mu;
+  std::map<std::tuple<int, int, int>, Entry> table;
+  static GemmTuner& get() {
+    static GemmTuner* t = new GemmTuner();   // process lifetime
+    return *t;
+  }
+};
+
+// returns the kernel (0 tcgen05, 1 mma.sync) and, when this launch is to be
+// timed, the two events to record around it
+static int gemm_pick(double avg_chunks, double flops, cudaEvent_t& e0, cudaEvent_t& e1) {
+  e0 = e1 = nullptr;
+  const int rule = avg_chunks >= 4.0 ? 0 : 1;
+  if (gemm_mode() == 1) return 0;
+  if (gemm_mode() == 2) return 1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int cb = std::min(6, (int)std::floor(std::log2(std::max(1.0, avg_chunks))));
+  const int fb = std::min(12, (int)std::floor(std::log2(std::max(1.0, flops / 1e7))));
+  GemmTuner& T = GemmTuner::get();
+  std::lock_guard<std::mutex> g(T.mu);
+  GemmTuner::Entry& E = T.table[std::make_tuple(dev, cb, fb)];
+  if (E.choice >= 0) return E.choice;
+  for (int c = 0; c < 2; ++c)
+    if (E.pending[c] && !E.done[c]) {
+      const cudaError_t q = cudaEventQuery(E.ev[c][1]);
+      if (q == cudaSuccess) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, E.ev[c][0], E.ev[c][1]) == cudaSuccess && E.flops[c] > 0) {
+          E.per_flop[c] = ms / E.flops[c];
+          E.done[c] = true;
+        }
+        E.pending[c] = false;
+      } else if (q == cudaErrorNotReady && cudaPeekAtLastError() == cudaErrorNotReady) {
+        cudaGetLastError();          // a not-ready query is not an error of ours
+      }
+    }
+  if (E.done[0] && E.done[1]) {
+    E.choice = E.per_flop[0] <= E.per_flop[1] ? 0 : 1;
+    for (auto& pr : E.ev)
+      for (auto& e : pr)
+        if (e) cudaEventDestroy(e);
+    static const bool dbg = [] {
+      const char* v = std::getenv("SPAND_DEBUG");
+      return v && v[0] == '1';
+    }();
+    if (dbg)
+      std::fprintf(stderr, "spand: GEMM class (k-chunks 2^%d, flops 2^%d x 1e7): tcgen05 %.3g, mma.sync %.3g ms/GF -> %s\n",
+                   cb, fb, E.per_flop[0] * 1e9, E.per_flop[1] * 1e9, E.choice == 0 ? "tcgen05" : "mma.sync");
+    return E.choice;
+  }
+  for (int c = 0; c < 2; ++c)
+    if (!E.done[c] && !E.pending[c]) {
+      if (!E.ev[c][0]) {
+        if (cudaEventCreate(&E.ev[c][0]) != cudaSuccess || cudaEventCreate(&E.ev[c][1]) != cudaSuccess) {
+          cudaGetLastError();
+          return rule;
+        }
+      }
+      E.pending[c] = true;
+      E.flops[c] = flops;
+      e0 = E.ev[c][0];
+      e1 = E.ev[c][1];
+      return c;
+    }
+  return rule;                       // both measurements still in flight
 }
 
 template <typename T>
 static void launch_gemm(DevMem& tmp, const std::vector<GemmTask<T>>& tasks, const std::vector<GemmTerm<T>>& terms,
                         cudaStream_t st) {
-  // tcgen05 pays off when a tile runs several 32-wide k-chunks (its set-up --
-  // tensor-memory allocation, barriers, the accumulator read-back -- is then
-  // amortised); short-k products (LU trailing updates) stay on mma.sync
-  bool umma = std::is_same<T, float>::value && use_umma();
-  if (umma) {
-    double chunks = 0;
+  bool umma = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (std::is_same<T, float>::value) {
+    double chunks = 0, flops = 0;
     int ntask = 0;
     for (const auto& tk : tasks) {
       if (tk.m <= 0 || tk.n <= 0) continue;
-      for (int t = tk.t0; t < tk.t1; ++t) chunks += (terms[t].k + UM_BK - 1) / UM_BK;
+      for (int t = tk.t0; t < tk.t1; ++t) {
+        chunks += (terms[t].k + UM_BK - 1) / UM_BK;
+        flops += 2.0 * tk.m * (double)tk.n * terms[t].k;
+      }
       ++ntask;
     }
-    umma = ntask > 0 && chunks >= 4.0 * ntask;
+    if (ntask > 0) umma = gemm_pick(chunks / ntask, flops, e0, e1) == 0;
   }
   const int BM = umma ? UM_BM : 64, BN = umma ? UM_BN : 64;
   std::vector<TileItem> tiles;
@@ -269,6 +360,7 @@ static void launch_gemm(DevMem& tmp, const std::vector<GemmTask<T>>& tasks, cons
   if (tmp.err) return;
   note_launch();
   if constexpr (std::is_same<T, float>::value) {
+    if (e0) cudaEventRecord(e0, st);
     if (umma) {
       static std::atomic<uint64_t> attr{0};
       once_per_device(attr, [] { set_dyn_smem((const void*)k_gemm_umma, UM_SMEM_BYTES); });
@@ -276,6 +368,7 @@ static void launch_gemm(DevMem& tmp, const std::vector<GemmTask<T>>& tasks, cons
     } else {
       k_gemm_tc<3><<<(unsigned)tiles.size(), 128, 0, st>>>(dt, dm, dl);   // 3xTF32 on mma.sync
     }
+    if (e1) cudaEventRecord(e1, st);
   } else {
     k_gemm<T><<<(unsigned)tiles.size(), 256, 0, st>>>(dt, dm, dl);
   }
@@ -1446,7 +1539,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
     S.t_elim_gemm_ms += ev_read(ev_gm[D]);
     if (hflags[0] & 1) return SPAND_ERR_ZERO_PIVOT;   // the root cause when both are set
     if (hflags[0] & 2) return SPAND_ERR_NONFINITE;
-    if (std::is_same<T, float>::value && use_umma()) {
+    if (std::is_same<T, float>::value && gemm_mode() != 2) {
       int uf = 0;
       SPAND_CUDA_TRY(cudaMemcpyFromSymbol(&uf, g_umma_fail, sizeof(int)));
       if (uf) {
