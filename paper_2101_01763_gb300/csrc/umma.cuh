@@ -104,6 +104,57 @@ __global__ void __launch_bounds__(128, 2) k_gemm_umma(const GemmTask<float>* tas
   while (cur_t < tk.t1 && term_klim(terms[cur_t], i0, j0, UM_BM, UM_BN) <= 0) ++cur_t;
   int item = 0;
   bool failed = false;
+  // operand values of one k-chunk held in registers: this thread's A row (32 k)
+  // and half of one B column (16 k).  The loads of chunk i+1 are issued right
+  // after the MMAs of chunk i, so their latency overlaps the tensor-core work.
+  const int r = tid, gi = i0 + r;
+  const int c = tid & 63, half = tid >> 6, gj = j0 + c;
+  float x[UM_BK], y[16];
+  auto load_chunk = [&](int t_, int l_) {
+    const GemmTerm<float> tm = terms[t_];
+    const bool a_vec = tm.ta && ((tm.lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(tm.A) & 15) == 0) &&
+                       l_ + UM_BK <= tm.k;
+    if (a_vec && gi < tk.m) {
+      const float4* src = reinterpret_cast<const float4*>(tm.A + l_ + (size_t)gi * tm.lda);
+#pragma unroll
+      for (int q = 0; q < UM_BK / 4; ++q) {
+        const float4 f = src[q];
+        x[4 * q] = f.x;
+        x[4 * q + 1] = f.y;
+        x[4 * q + 2] = f.z;
+        x[4 * q + 3] = f.w;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < UM_BK; ++e) {
+        const int gl = l_ + e;
+        x[e] = (gi < tk.m && gl < tm.k) ? (tm.ta ? tm.A[gl + (size_t)gi * tm.lda] : tm.A[gi + (size_t)gl * tm.lda])
+                                        : 0.f;
+      }
+    }
+    const int kb = l_ + half * 16;
+    const bool b_vec = !tm.tb && ((tm.ldb & 3) == 0) && ((reinterpret_cast<uintptr_t>(tm.B) & 15) == 0) &&
+                       kb + 16 <= tm.k;
+    if (b_vec && gj < tk.n) {
+      const float4* src = reinterpret_cast<const float4*>(tm.B + kb + (size_t)gj * tm.ldb);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 f = src[q];
+        y[4 * q] = f.x;
+        y[4 * q + 1] = f.y;
+        y[4 * q + 2] = f.z;
+        y[4 * q + 3] = f.w;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int gl = kb + e;
+        y[e] = (gj < tk.n && gl < tm.k) ? (tm.tb ? tm.B[gj + (size_t)gl * tm.ldb] : tm.B[gl + (size_t)gj * tm.ldb])
+                                        : 0.f;
+      }
+    }
+  };
+  if (cur_t < tk.t1) load_chunk(cur_t, cur_l);
   while (cur_t < tk.t1) {
     const int s = item & 1;
     unsigned char* st = um + s * UM_STAGE_BYTES;
@@ -116,57 +167,8 @@ __global__ void __launch_bounds__(128, 2) k_gemm_umma(const GemmTask<float>* tas
         break;
       }
     }
-    // ---- stage op(A) rows i0..i0+127 and op(B) columns j0..j0+63 of k-chunk cur_l
-    const GemmTerm<float> tm = terms[cur_t];
+    // ---- split the chunk's values into TF32 hi / lo in the core-matrix layout
     {
-      // all global loads of the chunk are issued before any conversion, as
-      // 16-byte loads where k is the contiguous direction and alignment allows
-      // A: thread = row, 32 k values
-      const int r = tid, gi = i0 + r;
-      float x[UM_BK];
-      const bool a_vec = tm.ta && ((tm.lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(tm.A) & 15) == 0) &&
-                         cur_l + UM_BK <= tm.k;
-      if (a_vec && gi < tk.m) {
-        const float4* src = reinterpret_cast<const float4*>(tm.A + cur_l + (size_t)gi * tm.lda);
-#pragma unroll
-        for (int q = 0; q < UM_BK / 4; ++q) {
-          const float4 f = src[q];
-          x[4 * q] = f.x;
-          x[4 * q + 1] = f.y;
-          x[4 * q + 2] = f.z;
-          x[4 * q + 3] = f.w;
-        }
-      } else {
-#pragma unroll
-        for (int e = 0; e < UM_BK; ++e) {
-          const int gl = cur_l + e;
-          x[e] = (gi < tk.m && gl < tm.k) ? (tm.ta ? tm.A[gl + (size_t)gi * tm.lda] : tm.A[gi + (size_t)gl * tm.lda])
-                                          : 0.f;
-        }
-      }
-      // B^T: threads 0..63 = columns (k 0..15), threads 64..127 the same columns (k 16..31)
-      const int c = tid & 63, half = tid >> 6, gj = j0 + c, kb = cur_l + half * 16;
-      float y[16];
-      const bool b_vec = !tm.tb && ((tm.ldb & 3) == 0) && ((reinterpret_cast<uintptr_t>(tm.B) & 15) == 0) &&
-                         kb + 16 <= tm.k;
-      if (b_vec && gj < tk.n) {
-        const float4* src = reinterpret_cast<const float4*>(tm.B + kb + (size_t)gj * tm.ldb);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float4 f = src[q];
-          y[4 * q] = f.x;
-          y[4 * q + 1] = f.y;
-          y[4 * q + 2] = f.z;
-          y[4 * q + 3] = f.w;
-        }
-      } else {
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const int gl = kb + e;
-          y[e] = (gj < tk.n && gl < tm.k) ? (tm.tb ? tm.B[gj + (size_t)gl * tm.ldb] : tm.B[gl + (size_t)gj * tm.ldb])
-                                          : 0.f;
-        }
-      }
 #pragma unroll
       for (int kq = 0; kq < UM_BK; kq += 4) {
         uint4 hi, lo;
@@ -234,6 +236,7 @@ __global__ void __launch_bounds__(128, 2) k_gemm_umma(const GemmTask<float>* tas
       ++cur_t;
       cur_l = 0;
     }
+    if (cur_t < tk.t1) load_chunk(cur_t, cur_l);   // overlaps the MMAs just issued
   }
   // ---- wait for the last committed chunk (it tracks every earlier MMA of the thread)
   if (item > 0 && !failed) {
