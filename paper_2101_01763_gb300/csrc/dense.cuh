@@ -89,6 +89,17 @@ __device__ inline void argmax_pair(T& v, int& i, T v2, int i2) {
   }
 }
 
+// argmax over the 32 lanes of a warp (largest value, lowest index on ties)
+template <typename T>
+__device__ inline void warp_argmax(T& v, int& i) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const T v2 = __shfl_xor_sync(0xffffffffu, v, o);
+    const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
+    argmax_pair(v, i, v2, i2);
+  }
+}
+
 template <typename T>
 __device__ inline void block_argmax(T& v, int& idx, T* sv, int* si) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -240,16 +251,22 @@ __global__ void __launch_bounds__(256) k_getrf_panel_smem(const MatRef<T>* mats,
     P[idx] = A[(k0 + r) + (size_t)(k0 + c) * ld];
   }
   __syncthreads();
-  for (int j = 0; j < jb; ++j) {
+  // pivot of column 0; later columns get theirs from the rank-1 update pass
+  // (each thread tracks |P(i, j+1)| of its rows as it updates them)
+  int p;
+  {
     T best = -1;
     int bi = m;
-    for (int i = j + threadIdx.x; i < m; i += blockDim.x) {
-      T a = fabs(P[i + j * m]);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      T a = fabs(P[i]);
       if (a != a) a = (T)INFINITY;
       argmax_pair(best, bi, a, i);
     }
     block_argmax(best, bi, sv, si);
-    const int p = bi;
+    p = bi;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = 0; j < jb; ++j) {
     if (threadIdx.x == 0) {
       M.ipiv[k0 + j] = k0 + p;
       piv_loc[j] = p;
@@ -262,19 +279,36 @@ __global__ void __launch_bounds__(256) k_getrf_panel_smem(const MatRef<T>* mats,
     }
     __syncthreads();
     const T pv = P[j + j * m];
-    if (!(pv == pv) || isinf(pv)) {
-      if (threadIdx.x == 0) atomicOr(flags, 2);
-    } else if (pv == (T)0) {
-      if (threadIdx.x == 0) atomicOr(flags, 1);
-    } else {
-      for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
+    const bool bad = !(pv == pv) || isinf(pv) || pv == (T)0;
+    if (threadIdx.x == 0 && bad) atomicOr(flags, (pv == (T)0) ? 1 : 2);
+    T best = -1;
+    int bi = m;
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
+      if (!bad) {
         const T l = P[i + j * m] / pv;
         P[i + j * m] = l;
         for (int c = j + 1; c < jb; ++c) P[i + c * m] -= l * P[j + c * m];
       }
+      if (j + 1 < jb) {
+        T a = fabs(P[i + (j + 1) * m]);
+        if (a != a) a = (T)INFINITY;
+        argmax_pair(best, bi, a, i);
+      }
+    }
+    warp_argmax(best, bi);
+    if (lane == 0) {
+      sv[wid] = best;
+      si[wid] = bi;
     }
     __syncthreads();
+    // every thread combines the warps' candidates (read before the next
+    // iteration's first barrier, written only after it)
+    T b2 = -1;
+    int i2 = m;
+    for (int w = 0; w < nw; ++w) argmax_pair(b2, i2, sv[w], si[w]);
+    p = i2;
   }
+  __syncthreads();
   for (int idx = threadIdx.x; idx < m * jb; idx += blockDim.x) {
     const int r = idx % m, c = idx / m;
     A[(k0 + r) + (size_t)(k0 + c) * ld] = P[idx];
@@ -1166,17 +1200,6 @@ struct GroupX {
   }
   __device__ void finish() {}
 };
-
-// argmax over the 32 lanes of a warp (largest value, lowest index on ties)
-template <typename T>
-__device__ inline void warp_argmax(T& v, int& i) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const T v2 = __shfl_xor_sync(0xffffffffu, v, o);
-    const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
-    argmax_pair(v, i, v2, i2);
-  }
-}
 
 // sum over aligned groups of L lanes (L a power of two <= 32)
 template <typename T>
