@@ -1107,6 +1107,7 @@ template <typename T, int CS>
 struct ClusterX {
   static constexpr int kMax = CS;
   static constexpr bool kOneSync = true;  // every CTA reads the pivot column itself
+  static constexpr bool kPublishCol = false;
   cooperative_groups::cluster_group cl;
   T* cand_v;                              // [2]: proposals double-buffered by step parity
   int* cand_i;
@@ -1145,13 +1146,21 @@ constexpr int QR_GMAX = 256;     // largest CTA group of the cooperative variant
 
 template <typename T>
 struct GroupX {
+  // One barrier per pivot step: each CTA also writes its candidate column to a
+  // global slot before the barrier, so after it every CTA reads the winner's
+  // column and builds the reflector itself.  Proposals and slots are
+  // double-buffered by step parity.
   static constexpr int kMax = QR_GMAX;
-  static constexpr bool kOneSync = false;
+  static constexpr bool kOneSync = true;
+  static constexpr bool kPublishCol = true;
   int q, G;
-  T* prop_v;                 // G proposals of this group (global)
+  T* prop_v;                 // [2][QR_GMAX] proposals of this group (global)
   int* prop_i;
   GroupSync* gs;
   int* err;
+  T* slot;                   // [2][G][ns] candidate columns of this group (global)
+  int ns;
+  int par = 0;
   __device__ int rank() const { return q; }
   __device__ int size() const { return G; }
   __device__ bool sync() {
@@ -1169,12 +1178,12 @@ struct GroupX {
       } else {
         long it = 0;
         while (*vgen == g) {
-          if (++it > (1l << 22)) {          // ~0.5 s with the back-off below
+          if (++it > (1l << 22)) {          // well under a second with the back-off below
             atomicOr(err, 16);
             s_ok = 0;
             break;
           }
-          __nanosleep(100);
+          if (it > 2048) __nanosleep(64);   // spin first: the partners are resident and close
         }
       }
       __threadfence();
@@ -1183,20 +1192,22 @@ struct GroupX {
     return s_ok != 0;
   }
   __device__ void publish(T v, int i) {
-    prop_v[q] = v;
-    prop_i[q] = i;
+    prop_v[par * QR_GMAX + q] = v;
+    prop_i[par * QR_GMAX + q] = i;
   }
   __device__ void gather(int r, T& v, int& i) {
-    v = __ldcg(prop_v + r);
-    i = __ldcg(prop_i + r);
+    v = __ldcg(prop_v + par * QR_GMAX + r);
+    i = __ldcg(prop_i + par * QR_GMAX + r);
   }
-  __device__ void next_step() {}
+  __device__ T* col_out() { return slot + ((size_t)par * G + q) * ns; }
+  __device__ const T* col_in(int r) { return slot + ((size_t)par * G + r) * ns; }
+  __device__ void next_step() { par ^= 1; }
   template <typename U>
   __device__ U* remote(U* p, int) { return p; }
   __device__ void fetch_reflector(T* v, T* s_tau, const QrTask<T>& tk, int k, int n, int, int tid, int nt) {
     const T* col = tk.V + (size_t)k * n;
     for (int i = k + tid; i < n; i += nt) v[i] = __ldcg(col + i);
-    if (tid == 0) *s_tau = __ldcg(tk.tau + k);
+    if (tid == 0 && s_tau) *s_tau = __ldcg(tk.tau + k);
   }
   __device__ void finish() {}
 };
@@ -1275,6 +1286,12 @@ __device__ void qrcp_group(const QrTask<T>& tk, T eps, X& xc, unsigned char* sme
       int bi = c;
       for (int j = j0 + tid; j < j1; j += NT) argmax_pair(best, bi, tk.norm2[j], j);
       block_argmax(best, bi, red_v, red_i);
+      if constexpr (X::kPublishCol) {
+        if (bi < c) {
+          T* out = xc.col_out();
+          for (int i = tid; i < n; i += NT) out[i] = at(i, bi);
+        }
+      }
       if (tid == 0) xc.publish(best, bi);
     } else if (tid == 0) {
       xc.publish(s_prop_v, s_prop_i);
@@ -1312,7 +1329,10 @@ __device__ void qrcp_group(const QrTask<T>& tk, T eps, X& xc, unsigned char* sme
       // every CTA builds the same reflector from column p, read from the owner
       // (its shared memory through the cluster, or W in global memory); the
       // owner never touches a used column again, so no second barrier is needed
-      if (SMEM) {
+      if constexpr (X::kPublishCol) {
+        const T* src = xc.col_in(orank);
+        for (int i = k + tid; i < n; i += NT) v[i] = owner ? at(i, p) : __ldcg(src + i);
+      } else if (SMEM) {
         const T* ws_o = xc.remote(Ws, orank);
         const int pj = p - orank * chunk;
         for (int i = k + tid; i < n; i += NT) v[i] = ws_o[(size_t)i * chunk + pj];
@@ -1430,6 +1450,16 @@ __device__ void qrcp_group(const QrTask<T>& tk, T eps, X& xc, unsigned char* sme
       s_prop_i = i2;
     }
     xc.next_step();
+    if constexpr (X::kPublishCol) {
+      // the candidate column for the next step, rows k+1.., into this step
+      // parity's slot (read by the others after the next barrier)
+      __syncthreads();
+      const int jn = s_prop_i;
+      if (jn < c) {
+        T* out = xc.col_out();
+        for (int i = k + 1 + tid; i < n; i += NT) out[i] = at(i, jn);
+      }
+    }
   }
   if (q == 0 && tid == 0) *tk.rank = ok ? rank : 0;
   if (ok) xc.finish();
@@ -1455,10 +1485,14 @@ struct QrGroupDesc {
 
 template <typename T, bool SMEM, int NT>
 __global__ void __launch_bounds__(NT, 1) k_qrcp_group(const QrTask<T>* tasks, const QrGroupDesc* desc,
-                                                      T* prop_v, int* prop_i, GroupSync* gs, int* err, T eps) {
+                                                      T* prop_v, int* prop_i, GroupSync* gs, int* err, T* slots,
+                                                      int ns, T eps) {
   extern __shared__ unsigned char qr_smem3[];
   const QrGroupDesc d = desc[blockIdx.x];
-  GroupX<T> xc{d.q, d.G, prop_v + (size_t)d.task * QR_GMAX, prop_i + (size_t)d.task * QR_GMAX, gs + d.task, err};
+  // a group's CTAs are consecutive in the launch: its slots start at its first CTA
+  T* gslot = slots + (size_t)(blockIdx.x - d.q) * 2 * ns;
+  GroupX<T> xc{d.q, d.G, prop_v + (size_t)d.task * 2 * QR_GMAX, prop_i + (size_t)d.task * 2 * QR_GMAX,
+               gs + d.task, err, gslot, ns};
   const QrTask<T> tk = tasks[d.task];
   qrcp_group<T, SMEM, NT>(tk, eps, xc, qr_smem3, nullptr, nullptr, err);
 }

@@ -1272,13 +1272,20 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       }
       T* d_prop_v = nullptr;
       int* d_prop_i = nullptr;
+      T* d_slots = nullptr;
+      int slot_ns = 32;
       GroupSync* d_gs = nullptr;
       QrTask<T>* d_coop = nullptr;
       std::vector<QrGroupDesc*> d_desc;
       if (!q_coop.empty()) {
         d_coop = tmp.upload(q_coop);
-        d_prop_v = tmp.alloc<T>(q_coop.size() * QR_GMAX);
-        d_prop_i = tmp.alloc<int>(q_coop.size() * QR_GMAX);
+        d_prop_v = tmp.alloc<T>(q_coop.size() * 2 * QR_GMAX);
+        d_prop_i = tmp.alloc<int>(q_coop.size() * 2 * QR_GMAX);
+        // candidate-column slots, reused launch after launch (stream order)
+        int ncta = 0;
+        for (auto& cl : coop) ncta = std::max(ncta, (int)cl.desc.size());
+        for (auto& t : q_coop) slot_ns = std::max(slot_ns, (t.n + 31) & ~31);
+        d_slots = tmp.alloc<T>((size_t)ncta * 2 * slot_ns);
         d_gs = tmp.alloc<GroupSync>(q_coop.size());
         for (auto& cl : coop) d_desc.push_back(tmp.upload(cl.desc));
         if (tmp.err) return SPAND_ERR_NOMEM;
@@ -1351,10 +1358,10 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
           const QrGroupDesc* a1 = d_desc[li];
           if (coop[li].smem)
             SPAND_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_qrcp_group<T, true, QR_THREADS>, a0, a1, d_prop_v, d_prop_i,
-                                              d_gs, d_flags, (T)eps));
+                                              d_gs, d_flags, d_slots, slot_ns, (T)eps));
           else
             SPAND_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_qrcp_group<T, false, 1024>, a0, a1, d_prop_v, d_prop_i, d_gs,
-                                              d_flags, (T)eps));
+                                              d_flags, d_slots, slot_ns, (T)eps));
         }
       }
       ev_end(ev_qr[l]);
