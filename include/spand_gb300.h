@@ -194,8 +194,9 @@ typedef struct {
   double elim_gemm_flops;
   int elim_gemm_launches;
   /* per level: RRQR time (ms) and algorithmic bytes, and how many interfaces
-   * ran in each RRQR form: [0] 8-CTA cluster, [1] 16-CTA cluster (both with
-   * W in shared memory), [2] cooperative CTA group (W in shared memory),
+   * ran in each RRQR form: [0] cluster of 1 to 8 CTAs, [1] 16-CTA cluster
+   * (both with W in shared memory), [2] cooperative CTA group (W in shared
+   * memory),
    * [3] W streamed from L2 / HBM (cooperative CTA group or 16-CTA cluster) */
   double t_rrqr_level_ms[32];
   double rrqr_bytes_level[32];

@@ -872,23 +872,29 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
         }
     }
   } ev_guard{{&ev_qr, &ev_gm}};
-  cudaStream_t side = nullptr;
-  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
-  SPAND_CUDA_TRY(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
-  SPAND_CUDA_TRY(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
-  SPAND_CUDA_TRY(cudaEventCreateWithFlags(&join_ev, cudaEventDisableTiming));
+  // side streams for the RRQR launches of a level (one per cluster size), forked
+  // from and joined back to the factorization's stream
+  constexpr int kQrClasses = 5;                      // clusters of 1, 2, 4, 8, 16 CTAs
   struct SideGuard {
-    cudaStream_t s;
-    cudaEvent_t a, b;
+    cudaStream_t s[kQrClasses] = {};
+    cudaEvent_t join[kQrClasses] = {};
+    cudaEvent_t fork = nullptr;
     ~SideGuard() {
-      if (s) {
-        cudaStreamSynchronize(s);
-        cudaStreamDestroy(s);
+      for (int i = 0; i < kQrClasses; ++i) {
+        if (s[i]) {
+          cudaStreamSynchronize(s[i]);
+          cudaStreamDestroy(s[i]);
+        }
+        if (join[i]) cudaEventDestroy(join[i]);
       }
-      if (a) cudaEventDestroy(a);
-      if (b) cudaEventDestroy(b);
+      if (fork) cudaEventDestroy(fork);
     }
-  } side_guard{side, fork_ev, join_ev};
+  } sides;
+  for (int i = 0; i < kQrClasses; ++i) {
+    SPAND_CUDA_TRY(cudaStreamCreateWithFlags(&sides.s[i], cudaStreamNonBlocking));
+    SPAND_CUDA_TRY(cudaEventCreateWithFlags(&sides.join[i], cudaEventDisableTiming));
+  }
+  SPAND_CUDA_TRY(cudaEventCreateWithFlags(&sides.fork, cudaEventDisableTiming));
   std::vector<LevelRec<T>> recs(D + 1);
   size_t park_b_tot = 0, park_c_tot = 0;
   double flops = 0;
@@ -1179,25 +1185,60 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       const int cl16 = (cur_dev >= 0 && cur_dev < 64 && ((can16.load() >> cur_dev) & 1)) ? 1 : 0;
       // on-chip variants: chunk resident in shared memory with 8 or 16 CTAs;
       // the rest streams W from L2 / HBM
-      std::vector<QrTask<T>> q_sm8, q_sm16, q_gl, q_big;
-      size_t sm8_max = 0, sm16_max = 0, gl_max = 0;
-      // what each on-chip kernel can be given next to its static shared memory
-      const long long lim8 = set_dyn_smem((const void*)k_qrcp_cluster<T, true, QR_CS, QR_THREADS>, kQrSmemMax);
-      const long long lim16 =
-          cl16 ? set_dyn_smem((const void*)k_qrcp_cluster<T, true, 16, QR_THREADS>, kQrSmemMax) : -1;
+      // on-chip cluster forms: W's column chunks in shared memory on 1, 2, 4, 8
+      // or 16 CTAs.  Each interface starts at the smallest cluster that holds it;
+      // while the level's clusters leave SMs idle, the interface with the most
+      // W per CTA doubles its cluster (fewer CTAs per interface cost less
+      // barrier time per unit of work when the GPU is full; more CTAs shorten
+      // the critical path when it is not).
+      std::vector<QrTask<T>> q_gl, q_big;
+      size_t gl_max = 0;
+      const int csz[kQrClasses] = {1, 2, 4, 8, 16};
+      long long limc[kQrClasses];
+      limc[0] = set_dyn_smem((const void*)k_qrcp_cluster<T, true, 1, QR_THREADS>, kQrSmemMax);
+      limc[1] = set_dyn_smem((const void*)k_qrcp_cluster<T, true, 2, QR_THREADS>, kQrSmemMax);
+      limc[2] = set_dyn_smem((const void*)k_qrcp_cluster<T, true, 4, QR_THREADS>, kQrSmemMax);
+      limc[3] = set_dyn_smem((const void*)k_qrcp_cluster<T, true, QR_CS, QR_THREADS>, kQrSmemMax);
+      limc[4] = cl16 ? set_dyn_smem((const void*)k_qrcp_cluster<T, true, 16, QR_THREADS>, kQrSmemMax) : -1;
+      const int top_cls = cl16 ? 4 : 3;
+      std::vector<int> cls_of(qt.size(), -1);
+      long long ctas = 0;
       for (size_t k = 0; k < qt.size(); ++k) {
-        const size_t b8 = qrcp_smem_bytes<T>(qt[k].n, qt[k].c, QR_CS);
-        const size_t b16 = qrcp_smem_bytes<T>(qt[k].n, qt[k].c, 16);
-        if ((long long)b8 <= lim8) {
-          q_sm8.push_back(qt[k]);
-          sm8_max = std::max(sm8_max, b8);
-        } else if (cl16 && (long long)b16 <= lim16) {
-          q_sm16.push_back(qt[k]);
-          sm16_max = std::max(sm16_max, b16);
-        } else {
-          q_big.push_back(qt[k]);
+        for (int ci = 0; ci <= top_cls; ++ci)
+          if ((long long)qrcp_smem_bytes<T>(qt[k].n, qt[k].c, csz[ci]) <= limc[ci]) {
+            cls_of[k] = ci;
+            break;
+          }
+        if (cls_of[k] < 0) q_big.push_back(qt[k]);
+        else ctas += csz[cls_of[k]];
+      }
+      {
+        int nsm_dev = 0, devq = 0;
+        cudaGetDevice(&devq);
+        cudaDeviceGetAttribute(&nsm_dev, cudaDevAttrMultiProcessorCount, devq);
+        while (ctas < nsm_dev) {
+          int best = -1;
+          double bw = -1;
+          for (size_t k = 0; k < qt.size(); ++k)
+            if (cls_of[k] >= 0 && cls_of[k] < top_cls) {
+              const double w = (double)qt[k].n * qt[k].c / csz[cls_of[k]];
+              if (w > bw) {
+                bw = w;
+                best = (int)k;
+              }
+            }
+          if (best < 0) break;
+          ctas += csz[cls_of[best]];
+          ++cls_of[best];
         }
       }
+      std::vector<QrTask<T>> q_cls[kQrClasses];
+      size_t cls_bytes[kQrClasses] = {0, 0, 0, 0, 0};
+      for (size_t k = 0; k < qt.size(); ++k)
+        if (cls_of[k] >= 0) {
+          q_cls[cls_of[k]].push_back(qt[k]);
+          cls_bytes[cls_of[k]] = std::max(cls_bytes[cls_of[k]], qrcp_smem_bytes<T>(qt[k].n, qt[k].c, csz[cls_of[k]]));
+        }
       // too large for one cluster: CTA groups of cooperative launches, as many
       // groups per launch as fit on the GPU at once.  A group keeps W in
       // shared memory when its chunks fit (G <= the resident-CTA capacity);
@@ -1291,15 +1332,15 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
         if (tmp.err) return SPAND_ERR_NOMEM;
         SPAND_CUDA_TRY(cudaMemsetAsync(d_gs, 0, sizeof(GroupSync) * q_coop.size(), st));
       }
-      qf[0] = (int)q_sm8.size();
-      qf[1] = (int)q_sm16.size();
+      qf[0] = (int)(q_cls[0].size() + q_cls[1].size() + q_cls[2].size() + q_cls[3].size());
+      qf[1] = (int)q_cls[4].size();
       qf[2] = n_group_smem;
       qf[3] = n_group_stream + (int)q_gl.size();
       // task arrays are uploaded on st before the fork, so the side stream
       // never reads them ahead of their copies
       QrTask<T>* d_gl = q_gl.empty() ? nullptr : tmp.upload(q_gl);
-      QrTask<T>* d_sm16 = q_sm16.empty() ? nullptr : tmp.upload(q_sm16);
-      QrTask<T>* d_sm8 = q_sm8.empty() ? nullptr : tmp.upload(q_sm8);
+      QrTask<T>* d_cls[kQrClasses];
+      for (int ci = 0; ci < kQrClasses; ++ci) d_cls[ci] = q_cls[ci].empty() ? nullptr : tmp.upload(q_cls[ci]);
       if (tmp.err) return SPAND_ERR_NOMEM;
       auto launch_qr = [&](const QrTask<T>* dq, size_t count, cudaStream_t s2, int cs, int nt, size_t bytes,
                            auto kern) -> int {
@@ -1323,19 +1364,27 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
         return SPAND_OK;
       };
       ev_begin(ev_qr[l]);
-      // the streaming launch and the on-chip launches overlap on two streams
-      SPAND_CUDA_TRY(cudaEventRecord(fork_ev, st));
-      SPAND_CUDA_TRY(cudaStreamWaitEvent(side, fork_ev, 0));
+      // the streaming launch and the on-chip launches (one stream per cluster size) overlap
+      SPAND_CUDA_TRY(cudaEventRecord(sides.fork, st));
+      for (int ci = 0; ci < kQrClasses; ++ci) SPAND_CUDA_TRY(cudaStreamWaitEvent(sides.s[ci], sides.fork, 0));
       if (cl16)
         SPAND_TRY(launch_qr(d_gl, q_gl.size(), st, 16, 1024, gl_max, k_qrcp_cluster<T, false, 16, 1024>));
       else
         SPAND_TRY(launch_qr(d_gl, q_gl.size(), st, QR_CS, 1024, gl_max, k_qrcp_cluster<T, false, QR_CS, 1024>));
-      SPAND_TRY(launch_qr(d_sm16, q_sm16.size(), side, 16, QR_THREADS, sm16_max,
+      SPAND_TRY(launch_qr(d_cls[4], q_cls[4].size(), sides.s[4], 16, QR_THREADS, cls_bytes[4],
                           k_qrcp_cluster<T, true, 16, QR_THREADS>));
-      SPAND_TRY(launch_qr(d_sm8, q_sm8.size(), side, QR_CS, QR_THREADS, sm8_max,
+      SPAND_TRY(launch_qr(d_cls[3], q_cls[3].size(), sides.s[3], QR_CS, QR_THREADS, cls_bytes[3],
                           k_qrcp_cluster<T, true, QR_CS, QR_THREADS>));
-      SPAND_CUDA_TRY(cudaEventRecord(join_ev, side));
-      SPAND_CUDA_TRY(cudaStreamWaitEvent(st, join_ev, 0));
+      SPAND_TRY(launch_qr(d_cls[2], q_cls[2].size(), sides.s[2], 4, QR_THREADS, cls_bytes[2],
+                          k_qrcp_cluster<T, true, 4, QR_THREADS>));
+      SPAND_TRY(launch_qr(d_cls[1], q_cls[1].size(), sides.s[1], 2, QR_THREADS, cls_bytes[1],
+                          k_qrcp_cluster<T, true, 2, QR_THREADS>));
+      SPAND_TRY(launch_qr(d_cls[0], q_cls[0].size(), sides.s[0], 1, QR_THREADS, cls_bytes[0],
+                          k_qrcp_cluster<T, true, 1, QR_THREADS>));
+      for (int ci = 0; ci < kQrClasses; ++ci) {
+        SPAND_CUDA_TRY(cudaEventRecord(sides.join[ci], sides.s[ci]));
+        SPAND_CUDA_TRY(cudaStreamWaitEvent(st, sides.join[ci], 0));
+      }
       // cooperative CTA groups after the join, so that nothing else holds SMs
       // while a launch that needs all of its CTAs resident at once starts
       {
