@@ -27,7 +27,7 @@ METRIC = "spaND factor+s-step GMRES time to 1e-8 rel residual; mixed vs FP64 spe
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # DRAM bytes (read + write) of the RRQR kernels of one C2 mixed factorization,
 # per level, from the ncu capture summarised in profiles/ (null until measured)
-RRQR_TRAFFIC_PER_LEVEL = 63.1e6
+RRQR_TRAFFIC_PER_LEVEL = 63.2e6
 
 
 def parse():
