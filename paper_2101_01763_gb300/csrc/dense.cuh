@@ -665,88 +665,21 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmTask<float>* tasks, c
 }
 
 // ------------------------------------------------------------------ triangular inverses
-// Column tile [j0, j0+32) of L^-1 (unit lower); column k of L^-1 is stored at
-// column perm[k] of F, rows scaled by rs[i] when rs != null:
-//   F = diag(rs) L^-1 P^T.
+// A triangular inverse task: the LU factors, the n x n output and an optional
+// diagonal scale (rows of L^-1 by 1/d_i, columns of U^-1 by d_j).  perm is
+// unused here (the row permutation is folded into gather indices elsewhere).
 template <typename T>
 struct InvTask {
   const T* LU;       // n x n factors
   T* out;            // n x n output
-  const int* perm;   // lower: column placement
-  const T* dscale;   // optional: lower -> row scale 1/d_i ; upper -> column scale d_j
+  const int* perm;
+  const T* dscale;
   int n;
 };
 
 struct InvTile {
   int task, j0;
 };
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_inv_lower(const InvTask<T>* tasks, const InvTile* tiles) {
-  __shared__ T Ls[32][33];
-  __shared__ T Xs[32][33];
-  __shared__ T Acc[32][33];
-  const InvTile tl = tiles[blockIdx.x];
-  const InvTask<T> tk = tasks[tl.task];
-  const int n = tk.n, j0 = tl.j0, jb = min(32, n - j0);
-  const size_t ld = n;
-  // output column for local column c
-  __shared__ int ocol[32];
-  if (threadIdx.x < 32) ocol[threadIdx.x] = (threadIdx.x < jb) ? tk.perm[j0 + threadIdx.x] : 0;
-  __syncthreads();
-  // zero rows above j0
-  for (int idx = threadIdx.x; idx < j0 * jb; idx += blockDim.x) {
-    const int r = idx % j0, c = idx / j0;
-    tk.out[r + (size_t)ocol[c] * ld] = 0;
-  }
-  for (int r0 = j0; r0 < n; r0 += 32) {
-    const int rb = min(32, n - r0);
-    // Acc = sum_{q0 in [j0, r0)} L[r0:, q0:] X[q0:, :]
-    for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) Acc[idx % 32][idx / 32] = 0;
-    __syncthreads();
-    for (int q0 = j0; q0 < r0; q0 += 32) {
-      for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
-        const int r = idx % 32, c = idx / 32;
-        Ls[r][c] = (r < rb) ? tk.LU[(r0 + r) + (size_t)(q0 + c) * ld] : (T)0;
-        Xs[r][c] = (c < jb) ? tk.out[(q0 + r) + (size_t)ocol[c] * ld] : (T)0;
-      }
-      __syncthreads();
-      for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
-        const int r = idx % 32, c = idx / 32;
-        T s = 0;
-#pragma unroll 8
-        for (int q = 0; q < 32; ++q) s += Ls[r][q] * Xs[q][c];
-        Acc[r][c] += s;
-      }
-      __syncthreads();
-    }
-    // diagonal block: X[r0] = Ldiag^-1 (I_part - Acc)
-    for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
-      const int r = idx % 32, c = idx / 32;
-      Ls[r][c] = (r < rb && c < rb) ? tk.LU[(r0 + r) + (size_t)(r0 + c) * ld] : (T)0;
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      const int c = threadIdx.x;
-      if (c < jb) {
-        T x[32];
-#pragma unroll
-        for (int r = 0; r < 32; ++r) x[r] = ((r0 + r == j0 + c) ? (T)1 : (T)0) - Acc[r][c];
-#pragma unroll
-        for (int r = 1; r < 32; ++r) {
-          T s = x[r];
-#pragma unroll
-          for (int q = 0; q < r; ++q) s -= Ls[r][q] * x[q];
-          x[r] = s;
-        }
-#pragma unroll
-        for (int r = 0; r < 32; ++r)
-          if (r < rb) tk.out[(r0 + r) + (size_t)ocol[c] * ld] = x[r];
-      }
-    }
-    __syncthreads();
-  }
-}
 
 // Column tile [j0, j0+32) of U^-1 (non-unit upper), column j scaled by dscale[j].
 template <typename T>
@@ -949,164 +882,29 @@ __global__ void k_eye(const EyeTask<T>* tasks, int ntask) {
 }
 
 // ------------------------------------------------------------------ RRQR
-// Column-pivoted Householder QR of W (n x c) stopped at the first k with
-// |R_kk| <= eps |R_00| (or R_00 = 0); writes the rank, tau and the reflectors.
-// Column norms are recomputed exactly in the update pass.  Dynamic shared
-// memory holds the current reflector (n values).
-template <typename T>
-__global__ void __launch_bounds__(256) k_qrcp(const QrTask<T>* tasks, T eps) {
-  extern __shared__ unsigned char qr_smem[];
-  T* v = reinterpret_cast<T*>(qr_smem);
-  __shared__ T sv[32];
-  __shared__ int si[32];
-  __shared__ T s_tau;
-  const QrTask<T> tk = tasks[blockIdx.x];
-  const int n = tk.n, c = tk.c;
-  const size_t ld = n;
-  T* W = tk.W;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int j = wid; j < c; j += nw) {
-    T s = 0;
-    for (int i = lane; i < n; i += 32) {
-      T a = W[i + j * ld];
-      s += a * a;
-    }
-    s = warp_sum(s);
-    if (lane == 0) tk.norm2[j] = s;
-  }
-  __syncthreads();
-  const int kmax = min(n, c);
-  T nrm0 = 0;
-  int rank = kmax;
-  for (int k = 0; k < kmax; ++k) {
-    T best = -1;
-    int bi = c;
-    for (int j = k + threadIdx.x; j < c; j += blockDim.x) argmax_pair(best, bi, tk.norm2[j], j);
-    block_argmax(best, bi, sv, si);
-    const T nrm = sqrt(fmax(best, (T)0));
-    if (k == 0) nrm0 = nrm;
-    if (nrm0 == (T)0 || (k > 0 && nrm <= eps * nrm0)) {
-      rank = k;
-      break;
-    }
-    const int p = bi;
-    if (p != k) {
-      for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        T t = W[i + k * ld];
-        W[i + k * ld] = W[i + p * ld];
-        W[i + p * ld] = t;
-      }
-      if (threadIdx.x == 0) {
-        T t = tk.norm2[k];
-        tk.norm2[k] = tk.norm2[p];
-        tk.norm2[p] = t;
-      }
-    }
-    __syncthreads();
-    // Householder reflector of W[k:, k]
-    T part = 0;
-    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) {
-      T a = W[i + k * ld];
-      part += a * a;
-    }
-    const T sigma = block_sum(part, sv);
-    const T alpha = W[k + k * ld];
-    T tau = 0, beta = alpha, scale = 0;
-    if (sigma > (T)0) {
-      beta = -copysign(sqrt(alpha * alpha + sigma), alpha);
-      tau = (beta - alpha) / beta;
-      scale = (T)1 / (alpha - beta);
-    }
-    for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
-      T vi;
-      if (i == k) vi = (T)1;
-      else vi = W[i + k * ld] * scale;
-      v[i - k] = vi;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      W[k + k * ld] = beta;
-      tk.tau[k] = tau;
-      s_tau = tau;
-    }
-    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) W[i + k * ld] = v[i - k];
-    __syncthreads();
-    // apply H = I - tau v v^T to the trailing columns and refresh their norms
-    for (int j = k + 1 + wid; j < c; j += nw) {
-      T* col = W + j * ld;
-      T dot = 0;
-      for (int i = k + lane; i < n; i += 32) dot += v[i - k] * col[i];
-      dot = warp_sum(dot) * s_tau;
-      T s = 0;
-      for (int i = k + lane; i < n; i += 32) {
-        T a = col[i] - dot * v[i - k];
-        col[i] = a;
-        if (i > k) s += a * a;
-      }
-      s = warp_sum(s);
-      if (lane == 0) tk.norm2[j] = s;
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *tk.rank = rank;
-}
-
-// explicit Q_c = H_0 ... H_{r-1} [I_r; 0]  (n x r, ld = n)
-template <typename T>
-__global__ void __launch_bounds__(256) k_form_q(const QrTask<T>* tasks) {
-  const QrTask<T> tk = tasks[blockIdx.x];
-  const int n = tk.n, r = *tk.rank;
-  const size_t ld = n;
-  T* Q = tk.Q;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int idx = threadIdx.x; idx < n * r; idx += blockDim.x) {
-    const int i = idx % n, j = idx / n;
-    Q[i + (size_t)j * ld] = (i == j) ? (T)1 : (T)0;
-  }
-  __syncthreads();
-  for (int k = r - 1; k >= 0; --k) {
-    const T tau = tk.tau[k];
-    const T* vk = tk.W + (size_t)k * ld;   // v_k[k] = 1 implicit, below-diagonal stored
-    for (int j = k + wid; j < r; j += nw) {
-      T* col = Q + (size_t)j * ld;
-      T dot = 0;
-      for (int i = k + lane; i < n; i += 32) dot += ((i == k) ? (T)1 : vk[i]) * col[i];
-      dot = warp_sum(dot) * tau;
-      for (int i = k + lane; i < n; i += 32) col[i] -= dot * ((i == k) ? (T)1 : vk[i]);
-    }
-    __syncthreads();
-  }
-}
-
-// ------------------------------------------------------------------ RRQR, cluster version
-// Column-pivoted Householder QR of W (n x c, row-major) by a cluster of QR_CS
-// CTAs that split the columns into contiguous chunks.  Each step: every CTA
-// proposes its best remaining column (largest residual norm, lowest index on
-// ties); the proposals are exchanged through distributed shared memory; the
-// owner of the winner builds the Householder vector and the others copy it;
-// every CTA updates its own remaining columns and their norms.  Columns are
-// not moved: a used flag (norm set to -1) replaces the swap, which leaves the
-// reflectors and hence Q unchanged.  The factorization stops at the first k
-// with |R_kk| <= eps |R_00| (or R_00 = 0); columns whose initial norm is
-// already <= eps |R_00| can never be chosen before that and are dropped.
+// Column-pivoted Householder QR of W (n x c, row-major) by the CTAs of one
+// exchange group (a thread-block cluster of 1 to 16 CTAs, or a group of a
+// cooperative launch) that split the columns into contiguous chunks.  Each
+// step: every CTA proposes its best remaining column (largest residual norm,
+// lowest index on ties); after one barrier every CTA knows the winner, reads
+// its column from the owner and builds the same Householder vector; every CTA
+// updates its own remaining columns and their norms.  Columns are not moved: a
+// used flag (norm set to -1) replaces the swap, which leaves the reflectors and
+// hence Q unchanged.  The factorization stops at the first k with
+// |R_kk| <= eps |R_00| (or R_00 = 0); columns whose initial norm is already
+// <= eps |R_00| can never be chosen before that and are dropped.
 constexpr int QR_CS = 8;
 constexpr int QR_THREADS = 512;
 
-// SMEM = true: each CTA keeps its column chunk of W (n x chunk, row-major) in
-// shared memory for the whole factorization (dynamic shared memory holds the
-// reflector, then the chunk); SMEM = false: W stays in global memory.
-// Threads are laid out as (row segment, column): a group of CW consecutive
-// columns is processed by all NT/CW row segments, so narrow chunks still keep
-// every thread busy; partial dots and norms are combined in shared memory.
 // How the CTAs that share one interface exchange the pivot proposals and the
-// reflector.  ClusterX: one thread-block cluster, distributed shared memory
-// and cluster barriers.  GroupX: a group of CTAs of a cooperative launch,
-// global memory (read past L1) and a counting barrier per group whose wait is
-// bounded (on timeout it raises bit 4 of the error flags and the CTAs leave).
+// winner's column.  ClusterX: one thread-block cluster, distributed shared
+// memory and cluster barriers.  GroupX: a group of CTAs of a cooperative
+// launch, global memory (read past L1) and a counting barrier per group whose
+// wait is bounded (on timeout it raises bit 4 of the error flags and the CTAs
+// leave).
 template <typename T, int CS>
 struct ClusterX {
   static constexpr int kMax = CS;
-  static constexpr bool kOneSync = true;  // every CTA reads the pivot column itself
   static constexpr bool kPublishCol = false;
   cooperative_groups::cluster_group cl;
   T* cand_v;                              // [2]: proposals double-buffered by step parity
@@ -1129,12 +927,7 @@ struct ClusterX {
   __device__ void next_step() { par ^= 1; }
   template <typename U>
   __device__ U* remote(U* p, int r) { return cl.map_shared_rank(p, r); }
-  // copy rows k..n-1 of the owner's reflector and its tau into this CTA
-  __device__ void fetch_reflector(T* v, T* s_tau, const QrTask<T>&, int k, int n, int owner, int tid, int nt) {
-    const T* rv = cl.map_shared_rank(v, owner);
-    for (int i = k + tid; i < n; i += nt) v[i] = rv[i];
-    if (tid == 0) *s_tau = *cl.map_shared_rank(s_tau, owner);
-  }
+
   __device__ void finish() { cl.sync(); }   // no CTA leaves while another may read its shared memory
 };
 
@@ -1151,7 +944,6 @@ struct GroupX {
   // column and builds the reflector itself.  Proposals and slots are
   // double-buffered by step parity.
   static constexpr int kMax = QR_GMAX;
-  static constexpr bool kOneSync = true;
   static constexpr bool kPublishCol = true;
   int q, G;
   T* prop_v;                 // [2][QR_GMAX] proposals of this group (global)
@@ -1204,11 +996,7 @@ struct GroupX {
   __device__ void next_step() { par ^= 1; }
   template <typename U>
   __device__ U* remote(U* p, int) { return p; }
-  __device__ void fetch_reflector(T* v, T* s_tau, const QrTask<T>& tk, int k, int n, int, int tid, int nt) {
-    const T* col = tk.V + (size_t)k * n;
-    for (int i = k + tid; i < n; i += nt) v[i] = __ldcg(col + i);
-    if (tid == 0 && s_tau) *s_tau = __ldcg(tk.tau + k);
-  }
+
   __device__ void finish() {}
 };
 
@@ -1325,10 +1113,11 @@ __device__ void qrcp_group(const QrTask<T>& tk, T eps, X& xc, unsigned char* sme
     const int p = gi;
     const bool owner = (p >= j0 && p < j1);
     const int orank = p / chunk;
-    if constexpr (X::kOneSync) {
-      // every CTA builds the same reflector from column p, read from the owner
-      // (its shared memory through the cluster, or W in global memory); the
-      // owner never touches a used column again, so no second barrier is needed
+    // every CTA builds the same reflector from column p, read from the owner
+    // (its shared memory through the cluster, its published slot in a group,
+    // or W in global memory); the owner never touches a used column again, so
+    // no second barrier is needed
+    {
       if constexpr (X::kPublishCol) {
         const T* src = xc.col_in(orank);
         for (int i = k + tid; i < n; i += NT) v[i] = owner ? at(i, p) : __ldcg(src + i);
@@ -1363,37 +1152,6 @@ __device__ void qrcp_group(const QrTask<T>& tk, T eps, X& xc, unsigned char* sme
           tk.norm2[p] = -1;                // used
         }
       }
-      __syncthreads();
-    } else {
-      if (owner) {
-        // Householder vector of column p, rows k..n-1
-        T prt = 0;
-        for (int i = k + 1 + tid; i < n; i += NT) {
-          const T a = at(i, p);
-          prt += a * a;
-        }
-        const T sigma = block_sum(prt, red_v);
-        const T alpha = at(k, p);
-        T tau = 2, beta = -alpha, scale = 0;        // column already reduced: H = I - 2 e_k e_k^T
-        if (sigma > (T)0) {
-          beta = -copysign(sqrt(alpha * alpha + sigma), alpha);
-          tau = (beta - alpha) / beta;
-          scale = (T)1 / (alpha - beta);
-        }
-        for (int i = k + tid; i < n; i += NT) {
-          const T vi = (i == k) ? (T)1 : at(i, p) * scale;
-          v[i] = vi;
-          tk.V[(size_t)i + (size_t)k * n] = vi;
-        }
-        if (tid == 0) {
-          s_scal[0] = tau;
-          tk.tau[k] = tau;
-          tk.norm2[p] = -1;                // used
-        }
-      }
-      if (!(ok = xc.sync())) break;
-      // ---- copy the reflector from the owner
-      if (!owner) xc.fetch_reflector(v, &s_scal[0], tk, k, n, orank, tid, NT);
       __syncthreads();
     }
     const T tau = s_scal[0];
