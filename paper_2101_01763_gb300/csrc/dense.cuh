@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(256) k_getrf_panel(const MatRef<T>* mats, int 
 constexpr int LU_SMEM_BYTES = 160 * 1024;
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_getrf_panel_smem(const MatRef<T>* mats, int nmat, int k0, int* flags) {
+__global__ void __launch_bounds__(512) k_getrf_panel_smem(const MatRef<T>* mats, int nmat, int k0, int* flags) {
   extern __shared__ unsigned char lu_smem[];
   T* P = reinterpret_cast<T*>(lu_smem);          // panel, column-major m x jb (ld m)
   __shared__ T sv[32];

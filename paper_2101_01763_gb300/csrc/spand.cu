@@ -456,7 +456,7 @@ static void batched_getrf(DevMem& tmp, std::vector<MatRef<T>>& mats, int* d_flag
     if (ds && k0 < nsmall_max) {
       const size_t sm = (size_t)(nsmall_max - k0) * std::min(LU_NB, nsmall_max - k0) * sizeof(T);
       note_launch();
-      k_getrf_panel_smem<T><<<(unsigned)small.size(), 256, sm, st>>>(ds, (int)small.size(), k0, d_flags);
+      k_getrf_panel_smem<T><<<(unsigned)small.size(), 512, sm, st>>>(ds, (int)small.size(), k0, d_flags);
       // the panel's interchanges and U12 on the columns outside it, 32 columns per CTA
       std::vector<LuColTile> tl;
       for (int b = 0; b < (int)small.size(); ++b) {
