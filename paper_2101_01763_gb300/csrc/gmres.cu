@@ -579,7 +579,6 @@ int sstep_core(const bsr_matrix* A, spand_factor_t M, const double* b, double* x
   const double bn = sqrt(bn2);
   std::vector<std::complex<double>> shifts;
   std::vector<double> Bh((s + 1) * s, 0.0);
-  bool first_cycle = true;
   int iters = 0;
   double est_rel = INFINITY;
   while (status == SPAND_OK) {
@@ -685,7 +684,6 @@ int sstep_core(const bsr_matrix* A, spand_factor_t M, const double* b, double* x
         break;
       }
     }
-    first_cycle = false;
     while (!done && status == SPAND_OK) {
       if (pend && csP + 2 * s > mc) break;
       if (!pend && c + s > mc) break;

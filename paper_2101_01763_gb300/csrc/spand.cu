@@ -482,7 +482,7 @@ static void batched_getrf(DevMem& tmp, std::vector<MatRef<T>>& mats, int* d_flag
       const int n = m.n;
       if (k0 + LU_NB >= n) continue;
       const int jb = LU_NB, r = k0 + jb, rem = n - r;
-      GemmTerm<T> tm{m.A + r + (size_t)k0 * n, m.A + k0 + (size_t)r * n, n, n, jb, 0, 0};
+      GemmTerm<T> tm{m.A + r + (size_t)k0 * n, m.A + k0 + (size_t)r * n, n, n, jb, 0, 0, 0};
       GemmTask<T> tk{m.A + r + (size_t)r * n, n, rem, rem, (T)-1, (T)1, (int)terms.size(), (int)terms.size() + 1};
       terms.push_back(tm);
       tasks.push_back(tk);
@@ -728,7 +728,7 @@ __global__ void k_level0_gather(const double* val, const int* row_of, const int*
 template <typename T>
 static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, int precision, FactorT<T>* F,
                        cudaStream_t st) {
-  const int D = P.D, K = P.K;
+  const int D = P.D;
   const int nsys = P.nsys;
   auto sysB = [&](int s) { return P.sys_B.empty() ? P.B : P.sys_B[s]; };
   auto sysE0 = [&](int s) { return P.sys_elem0.empty() ? 0 : P.sys_elem0[s]; };
@@ -1004,7 +1004,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
         const int a = kv.first.first, b = kv.first.second;
         const int t0 = (int)terms.size();
         for (int s : kv.second) {
-          terms.push_back({Xm.at({a, s}), Ym.at({s, b}), n[a], n[s], n[s], 0, 0});
+          terms.push_back({Xm.at({a, s}), Ym.at({s, b}), n[a], n[s], n[s], 0, 0, 0});
           flops += 2.0 * n[a] * (double)n[b] * n[s];
         }
         tasks.push_back({blk(a, b), n[a], n[a], n[b], (T)-1, (T)1, t0, (int)terms.size()});
@@ -1475,7 +1475,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
         T* G = tmp.alloc<T>((size_t)r * r);
         T* Tm = tmp.alloc<T>((size_t)r * r);
         T* M = tmp.alloc<T>((size_t)r * r);
-        gm.push_back({qt[q].V, qt[q].V, nn, nn, nn, 1, 0});
+        gm.push_back({qt[q].V, qt[q].V, nn, nn, nn, 1, 0, 0});
         gt.push_back({G, r, r, r, (T)1, (T)0, (int)gm.size() - 1, (int)gm.size()});
         wy.push_back({G, qt[q].tau, r});
         MatRef<T> mr;
@@ -1486,11 +1486,11 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
         tri.push_back(mr);
         Tinv.push_back(Tm);
         nod.push_back(nullptr);
-        mm.push_back({Tm, qt[q].V, r, nn, r, 0, 1});
+        mm.push_back({Tm, qt[q].V, r, nn, r, 0, 1, 0});
         mt.push_back({M, r, r, r, (T)1, (T)0, (int)mm.size() - 1, (int)mm.size()});
         SPAND_CUDA_TRY(cudaMemsetAsync(qt[q].Q, 0, sizeof(T) * (size_t)nn * r, st));
         eye_q.push_back({qt[q].Q, nn, r});
-        qm.push_back({qt[q].V, M, nn, r, r, 0, 0});
+        qm.push_back({qt[q].V, M, nn, r, r, 0, 0, 0});
         qtk.push_back({qt[q].Q, nn, nn, r, (T)-1, (T)1, (int)qm.size() - 1, (int)qm.size()});
       }
       if (tmp.err) return SPAND_ERR_NOMEM;
@@ -1565,9 +1565,9 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       }
       // both are sparsified (they have neighbours)
       T* Tm = tmp.alloc<T>((size_t)r[a] * n[b]);
-      m1.push_back({Qc[a], oblk(a, b), n[a], n[a], n[a], 1, 0});
+      m1.push_back({Qc[a], oblk(a, b), n[a], n[a], n[a], 1, 0, 0});
       t1.push_back({Tm, r[a], r[a], n[b], (T)1, (T)0, (int)m1.size() - 1, (int)m1.size()});
-      m2.push_back({Tm, Qc[b], r[a], n[b], n[b], 0, 0});
+      m2.push_back({Tm, Qc[b], r[a], n[b], n[b], 0, 0, 0});
       t2.push_back({dst, n2[pa], r[a], r[b], (T)1, (T)0, (int)m2.size() - 1, (int)m2.size()});
       flops += 2.0 * n[a] * (double)n[b] * (r[a] + r[b]);
     }
