@@ -382,6 +382,22 @@ def main():
     fb = F.stats()["factor_bytes"]
     F.close()
     achieved = fb / (t_apply * 1e-3) / 1e9
+    # block SpMV (FP64): A's blocks and two vectors per launch; the L2 is flushed
+    # before every timed launch (A is smaller than the L2)
+    y = torch.empty_like(rhs)
+    sp_ms = []
+    for it in range(13):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sg.spmv(A, rhs, out=y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if it >= 3:
+            sp_ms.append(e0.elapsed_time(e1))
+    t_spmv = statistics.mean(sp_ms)
+    sp_bytes = A.nnzb * A.B * A.B * 8 + 2 * A.K * A.B * 8
+    sp_ach = sp_bytes / (t_spmv * 1e-3) / 1e9
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside
     h_val = A.val.cpu().pin_memory()
@@ -471,7 +487,10 @@ def main():
              "ms_per_launch": gm_ms},
             {"kernel": "spand_apply (k_gemv sweeps, FP32 factors)", "bound": "hbm", "achieved": achieved,
              "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "peak_kind": f"{pk_kind} hbm_gbs",
-             "bytes_per_launch": fb, "ms_per_launch": t_apply}],
+             "bytes_per_launch": fb, "ms_per_launch": t_apply},
+            {"kernel": "k_bsr_spmv (FP64 block SpMV, L2 flushed before each launch)", "bound": "hbm",
+             "achieved": sp_ach, "peak": hbm, "unit": "GB/s", "frac": sp_ach / hbm, "peak_kind": f"{pk_kind} hbm_gbs",
+             "bytes_per_launch": sp_bytes, "ms_per_launch": t_spmv}],
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
     }

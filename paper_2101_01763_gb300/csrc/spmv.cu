@@ -1,9 +1,8 @@
 // Block-CSR SpMV (FP64) and the tall-skinny vector kernels of s-step GMRES.
 //
 // bsr_spmv: y = A x for the DG block pattern (Algorithm 2, the SpMV of the
-// matrix-powers step).  Thread per output row; blocks are column-major so for
-// a fixed block column consecutive threads read consecutive doubles.  The
-// fused form y = sa*(A x) + a1*u1 + a2*u2 also gives residuals and the Newton
+// matrix-powers step).  Blocks are column-major so for a fixed block column
+// consecutive rows are consecutive doubles.  The fused form y = sa*(A x) + a1*u1 + a2*u2 also gives residuals and the Newton
 // recurrence v_{k+1} = A M^-1 v_k - theta v_k (+ Im(theta)^2 v_{k-1}).
 #include <algorithm>
 #include <cstdint>
@@ -13,32 +12,50 @@
 
 namespace spand {
 
+// y = sa * A x + a1 * u1 + a2 * u2 (u1, u2 optional).  Each row's columns are
+// split over the 8 warps of a CTA: a CTA owns 32 consecutive rows (lane = row,
+// so a warp reads 32 consecutive entries of a block column), warp w sums block
+// columns w*cs .. w*cs+cs-1 of every block of the row, and warp 0 adds the 8
+// partial sums: eight times as many threads as rows and an eighth of the
+// dependent loads per thread.
 __global__ void __launch_bounds__(256) k_bsr_spmv(int K, int B, const int* __restrict__ row_ptr,
-                                                  const int* __restrict__ col, const double* __restrict__ val,
-                                                  const double* __restrict__ x, double* __restrict__ y, double sa,
-                                                  double a1, const double* __restrict__ u1, double a2,
-                                                  const double* __restrict__ u2) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= (int64_t)K * B) return;
-  const int e = (int)(g / B), r = (int)(g % B);
-  const size_t bb = (size_t)B * B;
-  double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-  for (int k = row_ptr[e]; k < row_ptr[e + 1]; ++k) {
-    const double* blk = val + (size_t)k * bb + r;
-    const double* xv = x + (size_t)col[k] * B;
-    int c = 0;
-    for (; c + 4 <= B; c += 4) {
-      s0 += __ldg(blk + (size_t)c * B) * __ldg(xv + c);
-      s1 += __ldg(blk + (size_t)(c + 1) * B) * __ldg(xv + c + 1);
-      s2 += __ldg(blk + (size_t)(c + 2) * B) * __ldg(xv + c + 2);
-      s3 += __ldg(blk + (size_t)(c + 3) * B) * __ldg(xv + c + 3);
+                                                        const int* __restrict__ col, const double* __restrict__ val,
+                                                        const double* __restrict__ x, double* __restrict__ y,
+                                                        double sa, double a1, const double* __restrict__ u1,
+                                                        double a2, const double* __restrict__ u2) {
+  __shared__ double part[8][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t g = (int64_t)blockIdx.x * 32 + lane;
+  const int64_t N = (int64_t)K * B;
+  double s = 0;
+  if (g < N) {
+    const int e = (int)(g / B), r = (int)(g % B);
+    const size_t bb = (size_t)B * B;
+    const int cs = (B + 7) / 8, c0 = w * cs, c1 = min(B, c0 + cs);
+    double s1 = 0;
+    for (int k = row_ptr[e]; k < row_ptr[e + 1]; ++k) {
+      const double* blk = val + (size_t)k * bb + r;
+      const double* xv = x + (size_t)col[k] * B;
+      int c = c0;
+      for (; c + 2 <= c1; c += 2) {
+        s += __ldg(blk + (size_t)c * B) * __ldg(xv + c);
+        s1 += __ldg(blk + (size_t)(c + 1) * B) * __ldg(xv + c + 1);
+      }
+      if (c < c1) s += __ldg(blk + (size_t)c * B) * __ldg(xv + c);
     }
-    for (; c < B; ++c) s0 += __ldg(blk + (size_t)c * B) * __ldg(xv + c);
+    s += s1;
   }
-  double v = sa * ((s0 + s1) + (s2 + s3));
-  if (u1) v += a1 * u1[g];
-  if (u2) v += a2 * u2[g];
-  y[g] = v;
+  part[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && g < N) {
+    double t = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t += part[q][lane];
+    double v = sa * t;
+    if (u1) v += a1 * u1[g];
+    if (u2) v += a2 * u2[g];
+    y[g] = v;
+  }
 }
 
 // y = A^T x: row e' of A^T gathers block (e, e') of every neighbour e (symmetric pattern)
@@ -74,7 +91,8 @@ int spmv_fused(const bsr_matrix* A, const double* x, double* y, int transpose, d
   const unsigned g = (unsigned)((n + 255) / 256);
   note_launch();
   if (!transpose)
-    k_bsr_spmv<<<g, 256, 0, st>>>(A->K, A->B, A->row_ptr, A->col, A->val, x, y, sa, a1, u1, a2, u2);
+    k_bsr_spmv<<<(unsigned)((n + 31) / 32), 256, 0, st>>>(A->K, A->B, A->row_ptr, A->col, A->val, x, y, sa,
+                                                               a1, u1, a2, u2);
   else
     k_bsr_spmv_t<<<g, 256, 0, st>>>(A->K, A->B, A->row_ptr, A->col, A->val, x, y, sa, a1, u1, a2, u2);
   return cudaGetLastError() == cudaSuccess ? SPAND_OK : SPAND_ERR_CUDA;
