@@ -139,7 +139,7 @@ int spand_plan_sizes(spand_plan_t plan, int* K, int* D, int* n_nodes, int64_t* t
 int spand_plan_export(spand_plan_t plan, int* owner, int* node_level, int* table);
 
 /* ---------------------------------------------------------------- factor
- * spand_factor - Sec. 2.2.1 (Eqs. 9-11), level by level: eliminate interiors
+ * spand_factor - Sec. 2.2.1 (Eqs. 10-12), level by level: eliminate interiors
  * by row-pivoted block LU with Schur updates; scale every interface by its
  * own PLU with diag(U) split evenly (L~ = L|D|^1/2, U~ = |D|^-1/2 U); compute
  * every interface's column-pivoted Householder QR of [A_sn A_ns^T], keep the

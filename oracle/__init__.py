@@ -11,7 +11,7 @@ Modules and the passages they follow (arXiv 2101.01763):
            CFL time step; A = M/dtau + dR/du and b = -R (Eq. 5).
   nd       Sec. 2.2.1 and Sec. 3.3: nested dissection of the (i, j) element grid,
            interiors / separators / interfaces per level, merges.
-  spand    Sec. 2.2.1, Eqs. 9-11: per-level elimination, interface scaling and
+  spand    Sec. 2.2.1, Eqs. 10-12: per-level elimination, interface scaling and
            RRQR sparsification; the resulting preconditioner and its transpose.
   gmres    Algorithm 1 (classical GMRES) and Algorithm 2 (s-step GMRES with
            single-reduce re-orthogonalization, Newton basis, Sec. 3.4).

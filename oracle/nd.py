@@ -149,7 +149,7 @@ def symbolic_blocks(tree, levels):
     """Cluster-pair block pattern per level (before elimination), with fill-in.
 
     Returns a list over levels of sorted lists of (a, b) index pairs into
-    levels[l]; pairs follow the pattern rule of Eq. 9 (elimination of an
+    levels[l]; pairs follow the pattern rule of Eq. 10 (elimination of an
     interior couples every pair of its neighbours).
     """
     out = []

@@ -1,10 +1,10 @@
 """Sparsified nested dissection (spaND) factorization and apply (oracle).
 
 Follows Sec. 2.2.1 of arXiv 2101.01763 level by level, l = 0 .. D:
-  1. Eliminate the interiors of level l by row-pivoted block LU (Eq. 9):
+  1. Eliminate the interiors of level l by row-pivoted block LU (Eq. 10):
        A_ss = P L U,  Y_sn = L^-1 P^T A_sn,  X_ns = A_ns U^-1,
        A_nn <- A_nn - X_ns Y_sn for every pair of neighbours of s.
-  2. Scale every remaining cluster (interface) with its own PLU (Eq. 10),
+  2. Scale every remaining cluster (interface) with its own PLU (Eq. 11),
      splitting diag(U) evenly: with Dg = diag(U),
        L~ = L |Dg|^(1/2),  U~ = |Dg|^(-1/2) U,  A_ss = P L~ U~,
      then A_sn <- L~^-1 P^T A_sn, A_ns <- A_ns U~^-1 and A_ss <- I.
@@ -12,7 +12,7 @@ Follows Sec. 2.2.1 of arXiv 2101.01763 level by level, l = 0 .. D:
      SciPy) of W = [A_sn A_ns^T] (neighbour blocks in cluster order); keep the
      rank r = #{k : |R_kk| > eps |R_00|} (reading: the paper asks only for
      ||W_f|| = O(eps)).  Then compress every block: A_ij <- Q_ic^T A_ij Q_jc
-     (Eq. 11 and the text after it); the f parts are dropped.  An interface
+     (Eq. 12 and the text after it); the f parts are dropped.  An interface
      with no neighbours is left unsparsified.
   4. Merge the clusters into the next level's clusters.
 The product of the recorded operators is the preconditioner (A ~ prod F_i);
@@ -84,7 +84,7 @@ def factor(bsr, n_theta, n_r, D, eps, hierarchy=None):
     for l in range(D + 1):
         info = levels[l]
         alive = set(range(len(info)))
-        # ---- 1. eliminate interiors (Eq. 9)
+        # ---- 1. eliminate interiors (Eq. 10)
         for s in [i for i in range(len(info)) if info[i]["interior"]]:
             ns = sorted(n for (a, n) in blocks if a == s and n != s)
             ss = len(cl[s])
@@ -114,7 +114,7 @@ def factor(bsr, n_theta, n_r, D, eps, hierarchy=None):
         if l == D:
             assert not surv and not blocks
             break
-        # ---- 2. scale interfaces (Eq. 10)
+        # ---- 2. scale interfaces (Eq. 11)
         SL, SU = {}, {}
         for s in surv:
             perm, L, U = _lu(blocks[(s, s)])
@@ -131,7 +131,7 @@ def factor(bsr, n_theta, n_r, D, eps, hierarchy=None):
             M = _linv_pt(perm, L, blocks[(a, b)]) / d[:, None]
             U, db = SU[b]
             blocks[(a, b)] = _m_uinv(U, M) * db[None, :]
-        # ---- 3. all Q first, then compress (Eq. 11)
+        # ---- 3. all Q first, then compress (Eq. 12)
         Q, rank = {}, {}
         lvl_ranks = []
         for s in surv:

@@ -1,16 +1,16 @@
 // Batched dense kernels on variable-size column-major matrices (FP64 / FP32).
 //
 // These carry the per-level block operations of spaND (Sec. 2.2.1):
-//   * getrf: right-looking blocked LU with partial pivoting (Eq. 9, Eq. 10);
+//   * getrf: right-looking blocked LU with partial pivoting (Eq. 10, Eq. 11);
 //     one launch per 32-column panel (one CTA per matrix) followed by a
 //     grouped GEMM for the trailing update;
 //   * grouped GEMM: C = beta C + alpha sum_t op(A_t) op(B_t), one CTA per
 //     64x64 output tile, all terms of a target accumulated by that CTA
-//     (Schur updates of Eq. 9 without atomics);
+//     (Schur updates of Eq. 10 without atomics);
 //   * triangular inverses: L^-1 P^T and U^-1 (optionally with the scaling
-//     split of Eq. 10), one CTA per 32-column tile;
+//     split of Eq. 11), one CTA per 32-column tile;
 //   * column-pivoted Householder QR truncated at |R_kk| <= eps |R_00| (the
-//     rank-revealing QR of Eq. 11) and the explicit Q_c it defines;
+//     rank-revealing QR of Eq. 12) and the explicit Q_c it defines;
 //   * block copies / transposed copies / identity fills for gathers and merges.
 #pragma once
 #include <cooperative_groups.h>

@@ -1,4 +1,4 @@
-// spaND factorization and apply on the GPU (Sec. 2.2.1, Eqs. 9-11).
+// spaND factorization and apply on the GPU (Sec. 2.2.1, Eqs. 10-12).
 //
 // The host walks the levels of the plan; at each level every phase is one
 // batched launch over all clusters of the level:
@@ -924,7 +924,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
     for (auto& pr : L.pattern)
       if (pr.first != pr.second) nbr[pr.first].push_back(pr.second);
     mark(0);
-    // ================= 1. eliminate interiors (Eq. 9)
+    // ================= 1. eliminate interiors (Eq. 10)
     std::vector<int> I;
     for (int c = 0; c < nc; ++c)
       if (L.cl[c].interior && n[c] > 0) I.push_back(c);
@@ -1026,7 +1026,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       break;
     }
     mark(1);
-    // ================= 2. scale interfaces (Eq. 10)
+    // ================= 2. scale interfaces (Eq. 11)
     std::vector<int> Fc;
     for (int c = 0; c < nc; ++c)
       if (!L.cl[c].interior && n[c] > 0) Fc.push_back(c);
@@ -1092,7 +1092,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       launch_gemm(tmp, t2, m2, st);
     }
     mark(2);
-    // ================= 3. all Q first (Eq. 11): RRQR of [A_sn A_ns^T]
+    // ================= 3. all Q first (Eq. 12): RRQR of [A_sn A_ns^T]
     std::vector<QrTask<T>> qt;
     std::vector<int> qcl;
     std::vector<CopyTask<T>> cps;

@@ -1,4 +1,4 @@
-"""Pins for the spaND oracle (Sec. 2.2.1, Eqs. 9-11)."""
+"""Pins for the spaND oracle (Sec. 2.2.1, Eqs. 10-12)."""
 import numpy as np
 import pytest
 import scipy.linalg as sla
@@ -55,7 +55,7 @@ def test_transpose_apply_adjoint_identity(c1):
 
 
 def test_scaling_split_is_balanced_and_exact():
-    # Eq. 10: A_ss = P L~ U~ with |diag L~| = |diag U~| = |diag U|^(1/2)
+    # Eq. 11: A_ss = P L~ U~ with |diag L~| = |diag U~| = |diag U|^(1/2)
     rng = np.random.default_rng(1)
     A = rng.standard_normal((12, 12)) + 4 * np.eye(12)
     perm, L, U = spand._lu(A)
@@ -71,7 +71,7 @@ def test_scaling_split_is_balanced_and_exact():
 
 
 def test_sparsification_residual_bound():
-    # Eq. 11: ||[W_fn W_nf^T]||_2 <= eps |R_00| sqrt(n) for the relative RRQR cut
+    # Eq. 12: ||[W_fn W_nf^T]||_2 <= eps |R_00| sqrt(n) for the relative RRQR cut
     rng = np.random.default_rng(2)
     n, m = 30, 90
     U_, _ = np.linalg.qr(rng.standard_normal((n, n)))
