@@ -399,6 +399,27 @@ def main():
     sp_bytes = A.nnzb * A.B * A.B * 8 + 2 * A.K * A.B * 8
     sp_ach = sp_bytes / (t_spmv * 1e-3) / 1e9
 
+    # ---- the pseudo-time continuation around the step (Eq. 9 CFL ramp; the ND plan is
+    # reused and A is re-assembled and re-factored at every step), mixed form
+    mopts = dict(cfl0=c.cfl, cfl_inf=1e6, rtol=0.0, eps=c.eps, precision="mixed", s=c.s, restart=c.restart,
+                 tol=c.tol, max_iters=c.max_iters)
+    try:
+        sg.march(Xd, c.p, ud, c.mach, c.alpha_deg, plan, max_steps=1, **mopts)
+        nm = 5
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        _, hm = sg.march(Xd, c.p, ud, c.mach, c.alpha_deg, plan, max_steps=nm, **mopts)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tm = e0.elapsed_time(e1)
+        march = {"pseudo_time_steps": hm["steps"], "ms": tm, "ms_per_pseudo_time_step": tm / max(1, hm["steps"]),
+                 "per_step": "assemble + ||R|| + spand_factor + s-step GMRES + update (and the final assembly)",
+                 "cfl0": c.cfl, "cfl_inf": 1e6, "res_norm": [float(v) for v in hm["res"]],
+                 "cfl": [float(v) for v in hm["cfl"]], "gmres_iters": [int(v) for v in hm["gmres_iters"]]}
+    except Exception as ex:   # reported, never fatal to the headline line
+        march = {"error": str(ex)}
+
     # ---- end to end through the C ABI with host buffers (pinned), copies inside
     h_val = A.val.cpu().pin_memory()
     h_rp = A.row_ptr.cpu().pin_memory()
@@ -491,6 +512,7 @@ def main():
             {"kernel": "k_bsr_spmv (FP64 block SpMV, L2 flushed before each launch)", "bound": "hbm",
              "achieved": sp_ach, "peak": hbm, "unit": "GB/s", "frac": sp_ach / hbm, "peak_kind": f"{pk_kind} hbm_gbs",
              "bytes_per_launch": sp_bytes, "ms_per_launch": t_spmv}],
+        "pseudo_time_march": march,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
     }

@@ -301,6 +301,63 @@ int sstep_gmres_solve_noalloc(const bsr_matrix* A, spand_factor_t M, const doubl
                               const gmres_opts* opts, gmres_stats* stats, cudaStream_t stream);
 size_t sstep_gmres_noalloc_capacity(void);
 
+/* ---------------------------------------------------------------- pseudo-time march
+ * dg_pseudo_time_march - the continuation of Sec. 2.1.2 around the solve:
+ * for n = 0, 1, ... assemble rhs = -R^n and A^n = M/dtau^n + dR/du|^n at
+ * CFL^n (dg_assemble_jacobian, Eqs. 5-8), factor A^n with spaND on the
+ * plan made once for the grid (the ordering is computed in preprocessing and
+ * the factorization redone at every nonlinear step, Sec. 3.3), solve
+ * A^n du = rhs by s-step GMRES from du = 0, and set u^{n+1} = u^n + du, with
+ * the CFL number ramped by the residual ratio (Eq. 9):
+ *     CFL^0 = flow->cfl,
+ *     CFL^n = min(CFL^0 ||R^0|| / ||R^{n-1}||, CFL^inf)   (n >= 1),
+ * ||.|| the 2-norm of all N residual coefficients (CFL^inf when ||R^{n-1}||
+ * is 0).  The march stops, before solving, at the first n with
+ * ||R^n|| <= rtol ||R^0|| or at n = max_steps; the state reached is
+ * assembled once more so that its residual norm is reported.
+ *  - mesh, p, flow: as dg_assemble_jacobian; u_hat: device [K, (p+1)^2, 4]
+ *    doubles, in = u^0, out = the last state (also on error: the last
+ *    state whose update completed).
+ *  - plan: from spand_analyze(n_theta, n_r, 4 (p+1)^2, ...) of this grid.
+ *  - opts->gmres.transpose is ignored (forward solves only).
+ *  - hist (may be NULL; each array may be NULL): host arrays written for
+ *    n = 0..steps: res_norm[n] = ||R^n||, cfl[n] = CFL^n, dtau[n]; and
+ *    gmres_iters[n] for the steps < steps that were solved.  Arrays of
+ *    res_norm, cfl, dtau need max_steps + 1 entries, gmres_iters max_steps.
+ *    hist->steps = number of completed solves (updates).
+ * Device scratch (A, rhs, du: about nnzb B^2 + 3 N doubles) is allocated on
+ * the stream and released before return.  Synchronizes the stream at every
+ * step (the residual norm decides CFL^{n+1} and the stop).
+ * Errors: those of dg_assemble_jacobian, spand_factor and sstep_gmres_solve
+ * (SPAND_ERR_NOT_CONVERGED when a linear solve misses its tolerance; u_hat
+ * then holds the state before that step), SPAND_ERR_ARG (plan of another
+ * grid, cfl <= 0, cfl_inf < cfl, max_steps < 0), SPAND_ERR_NONFINITE. */
+typedef struct {
+  int max_steps;      /* pseudo-time steps (linear solves) at most            */
+  double cfl_inf;     /* CFL^inf of Eq. 9 (CFL^0 is flow->cfl)                */
+  double rtol;        /* stop once ||R^n|| <= rtol ||R^0||                    */
+  double eps;         /* spaND tolerance                                      */
+  int precision;      /* SPAND_FP64 or SPAND_MIXED                            */
+  gmres_opts gmres;   /* linear solver (tolerance relative to ||R^n||)        */
+} dg_march_opts;
+
+typedef struct {
+  int steps;          /* completed solves                                     */
+  double* res_norm;   /* host [max_steps + 1]                                 */
+  double* cfl;        /* host [max_steps + 1]                                 */
+  double* dtau;       /* host [max_steps + 1]                                 */
+  int* gmres_iters;   /* host [max_steps]                                     */
+} dg_march_history;
+
+int dg_pseudo_time_march(const dg_mesh* mesh, int p, double* u_hat, const dg_flow_params* flow,
+                         spand_plan_t plan, const dg_march_opts* opts, dg_march_history* hist,
+                         cudaStream_t stream);
+
+/* CFL^n of Eq. 9 from CFL^0, CFL^inf, ||R^0|| and ||R^{n-1}|| (the rule
+ * dg_pseudo_time_march applies; host only).  Returns CFL^inf when
+ * r_prev <= 0. */
+double dg_cfl_ramp(double cfl0, double cfl_inf, double r0, double r_prev);
+
 const char* spand_status_string(int status);
 
 /* Number of kernel launches this library has issued in the process so far

@@ -62,6 +62,16 @@ class GmresStats(C.Structure):
                 ("t_small_ms", C.c_double)]
 
 
+class DgMarchOpts(C.Structure):
+    _fields_ = [("max_steps", C.c_int), ("cfl_inf", C.c_double), ("rtol", C.c_double), ("eps", C.c_double),
+                ("precision", C.c_int), ("gmres", GmresOpts)]
+
+
+class DgMarchHistory(C.Structure):
+    _fields_ = [("steps", C.c_int), ("res_norm", C.c_void_p), ("cfl", C.c_void_p), ("dtau", C.c_void_p),
+                ("gmres_iters", C.c_void_p)]
+
+
 EXPORTS = {
     "dg_assemble_jacobian": ([C.POINTER(DgMesh), C.c_int, C.c_void_p, C.POINTER(DgFlow), C.c_void_p,
                               C.POINTER(BsrMatrix), C.POINTER(C.c_double), C.c_void_p], C.c_int),
@@ -88,6 +98,9 @@ EXPORTS = {
     "sstep_gmres_solve_noalloc": ([C.POINTER(BsrMatrix), C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.POINTER(GmresOpts), C.POINTER(GmresStats), C.c_void_p], C.c_int),
     "sstep_gmres_noalloc_capacity": ([], C.c_size_t),
+    "dg_pseudo_time_march": ([C.POINTER(DgMesh), C.c_int, C.c_void_p, C.POINTER(DgFlow), C.c_void_p,
+                              C.POINTER(DgMarchOpts), C.POINTER(DgMarchHistory), C.c_void_p], C.c_int),
+    "dg_cfl_ramp": ([C.c_double, C.c_double, C.c_double, C.c_double], C.c_double),
     "spand_status_string": ([C.c_int], C.c_char_p),
     "spand_kernel_launches": ([], C.c_uint64),
 }

@@ -254,6 +254,39 @@ def pattern_outer(A, u, v, alpha=1.0, out=None, stream=None):
     return o
 
 
+def cfl_ramp(cfl0, cfl_inf, r0, r_prev):
+    """dg_cfl_ramp: CFL^n = min(CFL^0 ||R^0|| / ||R^{n-1}||, CFL^inf) (Eq. 9)."""
+    return float(L.lib().dg_cfl_ramp(float(cfl0), float(cfl_inf), float(r0), float(r_prev)))
+
+
+def march(nodes, p, u_hat, mach, alpha_deg, plan, cfl0=10.0, cfl_inf=1e6, max_steps=20, rtol=1e-10, eps=1e-3,
+          precision="mixed", s=4, restart=60, tol=1e-10, max_iters=400, basis="newton", gamma=1.4, bc="wall",
+          stream=None):
+    """dg_pseudo_time_march from u_hat (not modified): returns (u, history dict).
+
+    history: res (||R^n||, n = 0..steps), cfl, dtau, gmres_iters (per solve), steps.
+    """
+    _need(nodes, torch.float64, "nodes")
+    _need(u_hat, torch.float64, "u_hat")
+    n_r, n_theta = nodes.shape[0] - 1, nodes.shape[1]
+    u = u_hat.clone()
+    mesh = L.DgMesh(n_theta, n_r, nodes.data_ptr())
+    flow = L.DgFlow(gamma, mach, alpha_deg, cfl0, L.BC_WALL if bc == "wall" else L.BC_FARFIELD)
+    go = L.GmresOpts(s, restart, tol, max_iters, L.BASIS_NEWTON if basis == "newton" else L.BASIS_MONOMIAL, 0)
+    opts = L.DgMarchOpts(int(max_steps), float(cfl_inf), float(rtol), float(eps),
+                         L.SPAND_FP64 if precision == "fp64" else L.SPAND_MIXED, go)
+    res = np.zeros(max_steps + 1)
+    cfl = np.zeros(max_steps + 1)
+    dts = np.zeros(max_steps + 1)
+    its = np.zeros(max(max_steps, 1), np.int32)
+    hist = L.DgMarchHistory(0, res.ctypes.data, cfl.ctypes.data, dts.ctypes.data, its.ctypes.data)
+    L.check(L.lib().dg_pseudo_time_march(C.byref(mesh), p, _ptr(u), C.byref(flow), plan.h, C.byref(opts),
+                                         C.byref(hist), _stream(stream)), "dg_pseudo_time_march")
+    n = hist.steps
+    return u, dict(steps=n, res=res[:n + 1].copy(), cfl=cfl[:n + 1].copy(), dtau=dts[:n + 1].copy(),
+                   gmres_iters=its[:n].copy())
+
+
 class SpandSolve(torch.autograd.Function):
     """x = A^-1 b by spaND-preconditioned s-step GMRES, differentiable in (A values, b).
 

@@ -22,7 +22,7 @@ def lib():
 def _header_functions():
     txt = open(os.path.join(ROOT, "include", "spand_gb300.h")).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(\w+)\s*\(", txt, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|double|size_t|uint64_t|const char\*)\s+(\w+)\s*\(", txt, flags=re.M)))
 
 
 def test_exports_every_declared_symbol(lib):
@@ -69,3 +69,41 @@ def test_analyze_rejects_bad_args(lib):
     assert lib.spand_analyze(3, 4, 16, 2, C.byref(h)) == -1
     assert lib.spand_analyze(16, 0, 16, 2, C.byref(h)) == -1
     assert lib.spand_analyze(16, 8, 16, 2, None) == -1
+
+
+def test_cfl_ramp_matches_oracle(lib):
+    """dg_cfl_ramp (host) against the oracle's Eq. 9, bit for bit."""
+    from oracle.march import cfl_ramp
+    from paper_2101_01763_gb300.api import cfl_ramp as ramp
+    rng = np.random.default_rng(9)
+    for _ in range(200):
+        c0 = 10 ** rng.uniform(-2, 4)
+        cinf = c0 * 10 ** rng.uniform(0, 6)
+        r0 = 10 ** rng.uniform(-8, 2)
+        rp = r0 * 10 ** rng.uniform(-12, 1)
+        assert ramp(c0, cinf, r0, rp) == cfl_ramp(c0, cinf, r0, rp)
+    assert ramp(10.0, 1e6, 1.0, 0.0) == 1e6 == cfl_ramp(10.0, 1e6, 1.0, 0.0)
+
+
+def test_march_rejects_bad_args(lib):
+    """Argument checks of dg_pseudo_time_march return before any device work
+    (the pointers below are never dereferenced)."""
+    from paper_2101_01763_gb300 import _lib as L
+    from paper_2101_01763_gb300.api import Plan
+    P = Plan(16, 8, 16, 2)
+    mesh = L.DgMesh(16, 8, 16)
+    go = L.GmresOpts(4, 40, 1e-10, 400, 0, 0)
+
+    def call(p=1, flow_cfl=10.0, cfl_inf=1e6, steps=5, plan=P, m=mesh):
+        flow = L.DgFlow(1.4, 0.5, 2.0, flow_cfl, 0)
+        opts = L.DgMarchOpts(steps, cfl_inf, 1e-10, 1e-3, 0, go)
+        return lib.dg_pseudo_time_march(C.byref(m) if m is not None else None, p, C.c_void_p(16),
+                                        C.byref(flow), plan.h, C.byref(opts), None, None)
+
+    assert call(p=2) == -1                       # plan built for B = 16, not 36
+    assert call(m=L.DgMesh(16, 4, 16)) == -1     # plan of another grid
+    assert call(flow_cfl=0.0) == -1
+    assert call(cfl_inf=5.0) == -1               # CFL^inf below CFL^0
+    assert call(steps=-1) == -1
+    assert call(m=None) == -1
+    assert call(p=4) == -8
