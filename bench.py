@@ -420,6 +420,32 @@ def main():
     except Exception as ex:   # reported, never fatal to the headline line
         march = {"error": str(ex)}
 
+    # ---- Krylov stress setting (eps = 1e-1, tolerance 1e-10, at most 100 steps): Algorithm 1
+    # (MGS GMRES) beside Algorithm 2 (s-step), with the solvers' own per-phase stream times
+    krylov = None
+    try:
+        Fs = sg.Factor(plan, A, 0.1, "mixed")
+        krylov = {"eps": 0.1, "tol": 1e-10, "max_iters": 100, "restart": 60, "s": c.s, "factor": "mixed"}
+        for name, call in (("gmres_mgs", lambda: sg.gmres(A, Fs, rhs, restart=60, tol=1e-10, max_iters=100)),
+                           ("sstep_gmres", lambda: sg.sstep_gmres(A, Fs, rhs, s=c.s, restart=60, tol=1e-10,
+                                                                  max_iters=100))):
+            call()
+            n0 = sg.kernel_launches()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            _, kst = call()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            krylov[name] = {"ms": e0.elapsed_time(e1), "iters": kst["iters"], "converged": kst["converged"],
+                            "true_relres": kst["true_relres"], "reductions": kst["reductions"],
+                            "launches": sg.kernel_launches() - n0,
+                            "phase_ms": {"spmv": kst["t_spmv_ms"], "apply": kst["t_apply_ms"],
+                                         "orth": kst["t_orth_ms"], "other": kst["t_small_ms"]}}
+        Fs.close()
+    except Exception as ex:
+        krylov = {"error": str(ex)}
+
     # ---- end to end through the C ABI with host buffers (pinned), copies inside
     h_val = A.val.cpu().pin_memory()
     h_rp = A.row_ptr.cpu().pin_memory()
@@ -513,6 +539,7 @@ def main():
              "achieved": sp_ach, "peak": hbm, "unit": "GB/s", "frac": sp_ach / hbm, "peak_kind": f"{pk_kind} hbm_gbs",
              "bytes_per_launch": sp_bytes, "ms_per_launch": t_spmv}],
         "pseudo_time_march": march,
+        "krylov_stress": krylov,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
     }

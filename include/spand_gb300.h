@@ -255,11 +255,29 @@ typedef struct {
   double orth_err;      /* max over cycles of ||Q^T Q - I||_F             */
   double shifts_re[16]; /* Newton shifts in Leja order                    */
   double shifts_im[16];
-  double t_spmv_ms, t_apply_ms, t_orth_ms, t_small_ms; /* phase times (events) */
+  /* Phase times (ms) of the solve's stream, from CUDA events at every phase
+   * boundary (the time from one boundary to the next is charged to the
+   * phase it opens, host round trips included): block SpMV; preconditioner
+   * apply; orthogonalization (inner products / Gram reductions, CGS or MGS
+   * updates, normalization); the rest (small dense work on the device:
+   * Hessenberg, Cholesky, Givens, least squares; host reads of residual
+   * estimates; solution update).  Zero in sstep_gmres_solve_noalloc.     */
+  double t_spmv_ms, t_apply_ms, t_orth_ms, t_small_ms;
 } gmres_stats;
 
 int sstep_gmres_solve(const bsr_matrix* A, spand_factor_t M, const double* b, double* x,
                       const gmres_opts* opts, gmres_stats* stats, cudaStream_t stream);
+
+/* gmres_solve - Algorithm 1: restarted GMRES with modified Gram-Schmidt
+ * Arnoldi and Givens rotations, right preconditioning (A M^-1 u = b,
+ * x = x0 + M^-1 Q y), the baseline of the s-step solver (Sec. 3.4).  Each
+ * column takes one apply, one SpMV and j+2 inner products (j+1 for MGS, one
+ * norm), each its own reduction; stats->reductions counts them.  Same
+ * arguments, convergence test (Givens estimate per column, true FP64
+ * residual at restarts) and errors as sstep_gmres_solve; opts->s and
+ * opts->basis are ignored; stats->shifts_* and orth_err are 0. */
+int gmres_solve(const bsr_matrix* A, spand_factor_t M, const double* b, double* x,
+                const gmres_opts* opts, gmres_stats* stats, cudaStream_t stream);
 
 /* sstep_gmres_solve_batched - nsys independent solves of sstep_gmres_solve
  * (host arrays of nsys: A, M (NULL or per-system handles, e.g. from

@@ -92,6 +92,8 @@ EXPORTS = {
     "spand_apply": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p], C.c_int),
     "sstep_gmres_solve": ([C.POINTER(BsrMatrix), C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(GmresOpts),
                            C.POINTER(GmresStats), C.c_void_p], C.c_int),
+    "gmres_solve": ([C.POINTER(BsrMatrix), C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(GmresOpts),
+                     C.POINTER(GmresStats), C.c_void_p], C.c_int),
     "sstep_gmres_solve_batched": ([C.c_int, C.POINTER(BsrMatrix), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                    C.POINTER(C.c_void_p), C.POINTER(GmresOpts), C.POINTER(GmresStats),
                                    C.POINTER(C.c_int), C.c_void_p], C.c_int),

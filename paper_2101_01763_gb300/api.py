@@ -236,11 +236,31 @@ def sstep_gmres(A, M, b, x0=None, s=4, restart=40, tol=1e-8, max_iters=400, basi
                                        C.byref(opts), C.byref(stt), _stream(stream))
     if status != L.OK and (status != -6 or raise_on_nonconvergence):
         L.check(status, "sstep_gmres_solve")
-    stats = dict(iters=stt.iters, restarts=stt.restarts, reductions=stt.reductions,
-                 true_relres=stt.true_relres, est_relres=stt.est_relres, orth_err=stt.orth_err,
-                 shifts=[complex(stt.shifts_re[k], stt.shifts_im[k]) for k in range(s)],
-                 converged=(status == L.OK))
+    stats = _gmres_stats(stt, status)
+    stats["shifts"] = [complex(stt.shifts_re[k], stt.shifts_im[k]) for k in range(s)]
     return x, stats
+
+
+def _gmres_stats(stt, status):
+    return dict(iters=stt.iters, restarts=stt.restarts, reductions=stt.reductions,
+                true_relres=stt.true_relres, est_relres=stt.est_relres, orth_err=stt.orth_err,
+                t_spmv_ms=stt.t_spmv_ms, t_apply_ms=stt.t_apply_ms, t_orth_ms=stt.t_orth_ms,
+                t_small_ms=stt.t_small_ms, converged=(status == L.OK))
+
+
+def gmres(A, M, b, x0=None, restart=40, tol=1e-8, max_iters=400, transpose=False, stream=None,
+          raise_on_nonconvergence=False):
+    """gmres_solve (Algorithm 1, MGS): returns (x, stats dict)."""
+    _need(b, torch.float64, "b")
+    x = torch.zeros_like(b) if x0 is None else x0.clone()
+    opts = L.GmresOpts(1, restart, tol, max_iters, L.BASIS_NEWTON, int(transpose))
+    stt = L.GmresStats()
+    st = A.struct()
+    status = L.lib().gmres_solve(C.byref(st), M.h if M is not None else None, _ptr(b), _ptr(x),
+                                 C.byref(opts), C.byref(stt), _stream(stream))
+    if status != L.OK and (status != -6 or raise_on_nonconvergence):
+        L.check(status, "gmres_solve")
+    return x, _gmres_stats(stt, status)
 
 
 def pattern_outer(A, u, v, alpha=1.0, out=None, stream=None):

@@ -465,7 +465,91 @@ struct GmresScratch {
   int* stat;
   const double** dZ;
   const double** dY;
+  bool timed = false;   // phase times by CUDA events (not in the no-allocation entry point)
 };
+
+// The solve's stream timeline split into phases: mark(p) records an event, and
+// the time from one mark to the next is charged to the earlier mark's phase
+// (so a host round trip is charged to the phase that ends in it).  Read once,
+// after the stream has been synchronized.
+enum { PH_SPMV = 0, PH_APPLY = 1, PH_ORTH = 2, PH_SMALL = 3 };
+struct PhaseClock {
+  cudaStream_t st = nullptr;
+  bool on = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ph;
+  void mark(int p) {
+    if (!on) return;
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      on = false;
+      return;
+    }
+    if (cudaEventRecord(e, st) != cudaSuccess) {
+      cudaGetLastError();
+      cudaEventDestroy(e);
+      on = false;
+      return;
+    }
+    ev.push_back(e);
+    ph.push_back(p);
+  }
+  void finish(gmres_stats& s) {
+    if (on && ev.size() >= 2 && cudaStreamSynchronize(st) == cudaSuccess) {
+      double t[4] = {0.0, 0.0, 0.0, 0.0};
+      for (size_t i = 0; i + 1 < ev.size(); ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) == cudaSuccess) t[ph[i]] += ms;
+        else cudaGetLastError();
+      }
+      s.t_spmv_ms = t[PH_SPMV];
+      s.t_apply_ms = t[PH_APPLY];
+      s.t_orth_ms = t[PH_ORTH];
+      s.t_small_ms = t[PH_SMALL];
+    }
+    release();
+  }
+  void release() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    ev.clear();
+    ph.clear();
+  }
+  ~PhaseClock() { release(); }
+};
+
+// <x, y> of two device vectors into *out (device): per-CTA partial sums in a
+// fixed order, then one CTA adds them (the inner products of the MGS Arnoldi).
+__global__ void __launch_bounds__(256) k_dot_partial(int64_t N, const double* __restrict__ x,
+                                                     const double* __restrict__ y, double* __restrict__ part) {
+  double v = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    v += x[i] * y[i];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __shared__ double w[8];
+  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < 8; ++k) t += w[k];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_dot_final(int nblk, const double* __restrict__ part,
+                                                   double* __restrict__ out) {
+  double v = 0.0;
+  for (int k = threadIdx.x; k < nblk; k += blockDim.x) v += part[k];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __shared__ double w[8];
+  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < 8; ++k) t += w[k];
+    out[0] = t;
+  }
+}
 
 struct GmresSizes {
   std::vector<size_t> small;  // doubles per small-matrix piece
@@ -546,6 +630,9 @@ int sstep_core(const bsr_matrix* A, spand_factor_t M, const double* b, double* x
   auto Pc = [&](int j) { return PV + (size_t)j * N; };
   auto Vc = [&](int j) { return PV + (size_t)(s + j) * N; };
   int status = SPAND_OK;
+  PhaseClock clk;
+  clk.st = st;
+  clk.on = sc.timed;
   auto applyM = [&](const double* in, double* out) -> int {
     if (!M) return cudaMemcpyAsync(out, in, N * sizeof(double), cudaMemcpyDeviceToDevice, st) == cudaSuccess
                        ? SPAND_OK : SPAND_ERR_CUDA;
@@ -583,13 +670,16 @@ int sstep_core(const bsr_matrix* A, spand_factor_t M, const double* b, double* x
   double est_rel = INFINITY;
   while (status == SPAND_OK) {
     // ---- true residual r = b - A x
+    clk.mark(PH_SPMV);
     status = spmv_fused(A, x, r, tr, -1.0, 1.0, b, 0.0, nullptr, st);
     if (status) break;
     hz = {r};
     hy = {r};
+    clk.mark(PH_ORTH);
     status = gram_run(S.scal + 2, 1);
     if (status) break;
     double rr;
+    clk.mark(PH_SMALL);
     status = read_scal(2, rr);
     if (status) break;
     const double beta = sqrt(rr);
@@ -612,6 +702,7 @@ int sstep_core(const bsr_matrix* A, spand_factor_t M, const double* b, double* x
     note_launch();
     k_small<<<1, 256, 0, st>>>(S, MODE_INIT, 0, 0);
     // q0 = r / beta  (scal[1] = beta after INIT)
+    clk.mark(PH_ORTH);
     status = scale_copy(N, r, Qc(0), S.scal + 1, 1, st);
     if (status) break;
     int c = 0;        // last final column
@@ -621,10 +712,13 @@ int sstep_core(const bsr_matrix* A, spand_factor_t M, const double* b, double* x
     int k_cols = 0;   // Hessenberg columns in this cycle
     if (newton && shifts.empty()) {
       for (int j = 0; j < s && !done; ++j) {
+        clk.mark(PH_APPLY);
         status = applyM(Qc(j), u);
         if (status) break;
+        clk.mark(PH_SPMV);
         status = spmv_fused(A, u, wv, tr, 1.0, 0.0, nullptr, 0.0, nullptr, st);
         if (status) break;
+        clk.mark(PH_ORTH);
         for (int i = 0; i <= j; ++i) {
           hz = {Qc(i)};
           hy = {wv};
@@ -638,11 +732,14 @@ int sstep_core(const bsr_matrix* A, spand_factor_t M, const double* b, double* x
         hy = {wv};
         status = gram_run(S.scal + 2, 1);
         if (status) break;
+        clk.mark(PH_SMALL);
         note_launch();
         k_small<<<1, 256, 0, st>>>(S, MODE_ARNOLDI, j, 0);
+        clk.mark(PH_ORTH);
         status = scale_copy(N, wv, Qc(j + 1), S.scal + 4, 1, st);
         if (status) break;
         double est;
+        clk.mark(PH_SMALL);
         status = read_scal(0, est);
         if (status) break;
         ++iters;
@@ -692,9 +789,11 @@ int sstep_core(const bsr_matrix* A, spand_factor_t M, const double* b, double* x
       for (int k = 0; k < s && !status; ++k) {
         const double* vk = (k == 0) ? w0 : Vc(k - 1);
         const double* vkm = (k == 0) ? nullptr : ((k == 1) ? w0 : Vc(k - 2));
+        clk.mark(PH_APPLY);
         status = applyM(vk, u);
         if (status) break;
         const std::complex<double> t = shifts[k];
+        clk.mark(PH_SPMV);
         status = spmv_fused(A, u, Vc(k), tr, 1.0, -t.real(), vk, t.imag() < 0 ? t.imag() * t.imag() : 0.0,
                             t.imag() < 0 ? vkm : nullptr, st);
       }
@@ -712,15 +811,18 @@ int sstep_core(const bsr_matrix* A, spand_factor_t M, const double* b, double* x
         hz.push_back(Vc(j));
         hy.push_back(Vc(j));
       }
+      clk.mark(PH_ORTH);
       status = gram_run(S.G, ldg);
       if (status) break;
       stl.reductions++;
       if (pend) {
+        clk.mark(PH_SMALL);
         note_launch();
         k_small<<<1, 256, 0, st>>>(S, MODE_PENDING, c, 0);
         status = check_status();
         if (status) break;
         // Q_P = P S2^-1 - Q_f CP  -> columns c+1..c+s
+        clk.mark(PH_ORTH);
         status = block_update(N, s, s, Pc(0), N, S.S2inv, c + 1, Qc(0), N, S.CP, ldh, Qc(c + 1), N, 0, st);
         if (status) break;
         const int c_old = c;
@@ -728,6 +830,7 @@ int sstep_core(const bsr_matrix* A, spand_factor_t M, const double* b, double* x
         iters += s;
         k_cols += s;
         double est;
+        clk.mark(PH_SMALL);
         status = read_scal(0, est);
         if (status) break;
         est_rel = est / bn;
@@ -737,13 +840,16 @@ int sstep_core(const bsr_matrix* A, spand_factor_t M, const double* b, double* x
           break;
         }
         // P' = V S1^-1 - Q_{0..c} CV  (into the P slot)
+        clk.mark(PH_ORTH);
         status = block_update(N, s, s, Vc(0), N, S.S1inv, c + 1, Qc(0), N, S.CV, ldh, Pc(0), N, 0, st);
         csP = c;
       } else {
+        clk.mark(PH_SMALL);
         note_launch();
         k_small<<<1, 256, 0, st>>>(S, MODE_FIRST, c, 0);
         status = check_status();
         if (status) break;
+        clk.mark(PH_ORTH);
         status = block_update(N, s, s, Vc(0), N, S.S1inv, c + 1, Qc(0), N, S.CV, ldh, Pc(0), N, 0, st);
         csP = c;
         pend = true;
@@ -759,24 +865,29 @@ int sstep_core(const bsr_matrix* A, spand_factor_t M, const double* b, double* x
         hz.push_back(Pc(j));
         hy.push_back(Pc(j));
       }
+      clk.mark(PH_ORTH);
       status = gram_run(S.G, ldg);
       if (status) break;
       stl.reductions++;
+      clk.mark(PH_SMALL);
       note_launch();
       k_small<<<1, 256, 0, st>>>(S, MODE_FLUSH, c, 0);
       status = check_status();
       if (status) break;
+      clk.mark(PH_ORTH);
       status = block_update(N, s, s, Pc(0), N, S.S2inv, c + 1, Qc(0), N, S.CP, ldh, Qc(c + 1), N, 0, st);
       if (status) break;
       c += s;
       iters += s;
       k_cols += s;
       double est;
+      clk.mark(PH_SMALL);
       status = read_scal(0, est);
       if (status) break;
       est_rel = est / bn;
     }
     // ---- orthogonality diagnostic ||Q^T Q - I||_F over the k+1 final columns
+    clk.mark(PH_SMALL);
     {
       const int kq = k_cols + 1;
       if (kq <= 32) {
@@ -800,14 +911,17 @@ int sstep_core(const bsr_matrix* A, spand_factor_t M, const double* b, double* x
       status = block_update(N, 1, 0, nullptr, N, nullptr, k_cols, Qc(0), N, S.y, k_cols, wv, N, 0, st);
       if (status) break;
       // block_update computes -Z y; negate through the M^-1 + axpy sign
+      clk.mark(PH_APPLY);
       status = applyM(wv, u);
       if (status) break;
+      clk.mark(PH_SMALL);
       status = axpy_dev(N, S.scal + 7, -1.0, u, x, st);   // scal[7] = 1
       if (status) break;
     }
     stl.restarts++;
     if (cudaGetLastError() != cudaSuccess) status = SPAND_ERR_CUDA;
   }
+  clk.mark(PH_SMALL);
   stl.iters = iters;
   stl.est_relres = est_rel;
   {
@@ -819,9 +933,188 @@ int sstep_core(const bsr_matrix* A, spand_factor_t M, const double* b, double* x
     stl.orth_err = o;
   }
   if (cudaStreamSynchronize(st) != cudaSuccess && status == SPAND_OK) status = SPAND_ERR_CUDA;
+  clk.finish(stl);
   if (stats) *stats = stl;
   return status;
 }
+
+// Algorithm 1: restarted GMRES, modified Gram-Schmidt Arnoldi, Givens
+// rotations, right preconditioning.  Per column j: one preconditioner apply,
+// one SpMV, j+1 inner products each followed by its axpy (MGS), one norm, the
+// Givens update (k_small) and a host read of the residual estimate.  Every
+// inner product is a separate reduction; that is the cost s-step GMRES
+// removes.  Same scratch layout as the s-step solve with s = 1.
+int mgs_core(const bsr_matrix* A, spand_factor_t M, const double* b, double* x, const gmres_opts* opts,
+             gmres_stats* stats, cudaStream_t st, const GmresScratch& sc) {
+  const int m = opts->restart;
+  const int64_t N = (int64_t)A->K * A->B;
+  const int tr = opts->transpose ? 1 : 0;
+  gmres_stats stl;
+  memset(&stl, 0, sizeof(stl));
+  const int ldh = m + 1;
+  const GmresSizes zs = gmres_sizes(m, 1);
+  cudaMemsetAsync(sc.small, 0, zs.small_tot * sizeof(double), st);
+  cudaMemsetAsync(sc.stat, 0, 4 * sizeof(int), st);
+  Small S;
+  {
+    double* p = sc.small;
+    double** f[] = {&S.H, &S.R, &S.cs, &S.sn, &S.g, &S.B, &S.G, &S.R1P, &S.S1P, &S.t0P, &S.CP, &S.S2inv, &S.CV,
+                    &S.S1inv, &S.T, &S.Hn, &S.y, &S.scal, &S.M1};
+    for (size_t k = 0; k < zs.small.size(); ++k) {
+      *f[k] = p;
+      p += zs.small[k];
+    }
+  }
+  S.status = sc.stat;
+  S.m = m;
+  S.s = 1;
+  S.ldh = ldh;
+  S.ldg = m + 4;
+  S.ldt = m + 3;
+  double* Q = sc.vec;                          // N x (m+1), then 2 unused columns
+  double* r = sc.vec + (size_t)(m + 3) * N;
+  double* u = r + N;
+  double* wv = u + N;
+  auto Qc = [&](int j) { return Q + (size_t)j * N; };
+  const int nblk = (int)std::min<int64_t>(kGramBlocks, (N + 255) / 256);
+  PhaseClock clk;
+  clk.st = st;
+  clk.on = sc.timed;
+  auto dot = [&](const double* a, const double* c, double* out) -> int {
+    note_launch(2);
+    k_dot_partial<<<nblk, 256, 0, st>>>(N, a, c, sc.part);
+    k_dot_final<<<1, 256, 0, st>>>(nblk, sc.part, out);
+    return cudaGetLastError() == cudaSuccess ? SPAND_OK : SPAND_ERR_CUDA;
+  };
+  auto applyM = [&](const double* in, double* out) -> int {
+    if (!M) return cudaMemcpyAsync(out, in, N * sizeof(double), cudaMemcpyDeviceToDevice, st) == cudaSuccess
+                       ? SPAND_OK : SPAND_ERR_CUDA;
+    return factor_apply(M, in, out, tr, st);
+  };
+  double hs[8];
+  auto read_scal = [&]() -> int {   // scal[0..4] in one read
+    if (cudaMemcpyAsync(hs, S.scal, 5 * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess) return SPAND_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return SPAND_ERR_CUDA;
+    return SPAND_OK;
+  };
+  int status = dot(b, b, S.scal + 2);
+  if (status == SPAND_OK) status = read_scal();
+  const double bn = sqrt(hs[2]);
+  int iters = 0;
+  double est_rel = INFINITY;
+  while (status == SPAND_OK) {
+    // ---- true residual r = b - A x
+    clk.mark(PH_SPMV);
+    status = spmv_fused(A, x, r, tr, -1.0, 1.0, b, 0.0, nullptr, st);
+    if (status) break;
+    clk.mark(PH_ORTH);
+    status = dot(r, r, S.scal + 2);
+    if (status) break;
+    stl.reductions++;
+    clk.mark(PH_SMALL);
+    status = read_scal();
+    if (status) break;
+    const double beta = sqrt(hs[2]);
+    stl.true_relres = bn > 0 ? beta / bn : beta;
+    if (!std::isfinite(beta)) {
+      status = SPAND_ERR_NONFINITE;
+      break;
+    }
+    if (stl.true_relres <= opts->tol) break;
+    if (iters >= opts->max_iters) {
+      status = SPAND_ERR_NOT_CONVERGED;
+      break;
+    }
+    const int mc = std::min(m, opts->max_iters - iters);
+    note_launch();
+    k_small<<<1, 256, 0, st>>>(S, MODE_INIT, 0, 0);
+    clk.mark(PH_ORTH);
+    status = scale_copy(N, r, Qc(0), S.scal + 1, 1, st);   // q0 = r / beta
+    if (status) break;
+    int k_cols = 0;
+    for (int j = 0; j < mc; ++j) {
+      clk.mark(PH_APPLY);
+      status = applyM(Qc(j), u);
+      if (status) break;
+      clk.mark(PH_SPMV);
+      status = spmv_fused(A, u, wv, tr, 1.0, 0.0, nullptr, 0.0, nullptr, st);
+      if (status) break;
+      clk.mark(PH_ORTH);
+      for (int i = 0; i <= j && !status; ++i) {
+        double* hij = S.H + i + (size_t)j * ldh;
+        status = dot(Qc(i), wv, hij);
+        if (status == SPAND_OK) status = axpy_dev(N, hij, -1.0, Qc(i), wv, st);
+      }
+      if (status) break;
+      status = dot(wv, wv, S.scal + 2);
+      if (status) break;
+      stl.reductions += j + 2;
+      clk.mark(PH_SMALL);
+      note_launch();
+      k_small<<<1, 256, 0, st>>>(S, MODE_ARNOLDI, j, 0);
+      clk.mark(PH_ORTH);
+      status = scale_copy(N, wv, Qc(j + 1), S.scal + 4, 1, st);
+      if (status) break;
+      clk.mark(PH_SMALL);
+      status = read_scal();
+      if (status) break;
+      ++iters;
+      ++k_cols;
+      est_rel = hs[0] / bn;
+      if (!std::isfinite(est_rel)) {
+        status = SPAND_ERR_NONFINITE;
+        break;
+      }
+      if (est_rel <= opts->tol || hs[4] == 0.0) break;
+    }
+    if (status) break;
+    // ---- x += M^-1 (Q_{0:k} y)
+    clk.mark(PH_SMALL);
+    note_launch();
+    k_small<<<1, 256, 0, st>>>(S, MODE_SOLVE, k_cols, 0);
+    status = block_update(N, 1, 0, nullptr, N, nullptr, k_cols, Qc(0), N, S.y, k_cols, wv, N, 0, st);
+    if (status) break;
+    clk.mark(PH_APPLY);
+    status = applyM(wv, u);     // wv = -Q y
+    if (status) break;
+    clk.mark(PH_SMALL);
+    status = axpy_dev(N, S.scal + 7, -1.0, u, x, st);   // scal[7] = 1
+    if (status) break;
+    stl.restarts++;
+    if (cudaGetLastError() != cudaSuccess) status = SPAND_ERR_CUDA;
+  }
+  clk.mark(PH_SMALL);
+  stl.iters = iters;
+  stl.est_relres = est_rel;
+  if (cudaStreamSynchronize(st) != cudaSuccess && status == SPAND_OK) status = SPAND_ERR_CUDA;
+  clk.finish(stl);
+  if (stats) *stats = stl;
+  return status;
+}
+
+// Device scratch of one solve (released on the stream).
+struct OwnedScratch {
+  GmresScratch sc{};
+  cudaStream_t st = nullptr;
+  int alloc(const GmresSizes& zs, int64_t N, cudaStream_t s) {
+    st = s;
+    sc.timed = true;
+    if (cudaMallocAsync(&sc.small, zs.small_tot * sizeof(double), st) != cudaSuccess ||
+        cudaMallocAsync(&sc.vec, zs.nvec * N * sizeof(double), st) != cudaSuccess ||
+        cudaMallocAsync(&sc.part, zs.part * sizeof(double), st) != cudaSuccess ||
+        cudaMallocAsync(&sc.stat, 4 * sizeof(int), st) != cudaSuccess ||
+        cudaMallocAsync((void**)&sc.dZ, zs.maxptr * sizeof(double*), st) != cudaSuccess ||
+        cudaMallocAsync((void**)&sc.dY, 64 * sizeof(double*), st) != cudaSuccess) {
+      cudaGetLastError();
+      return SPAND_ERR_NOMEM;
+    }
+    return SPAND_OK;
+  }
+  ~OwnedScratch() {
+    for (void* p : {(void*)sc.small, (void*)sc.vec, (void*)sc.part, (void*)sc.stat, (void*)sc.dZ, (void*)sc.dY})
+      if (p) cudaFreeAsync(p, st);
+  }
+};
 
 }  // namespace
 }  // namespace spand
@@ -831,26 +1124,32 @@ extern "C" int sstep_gmres_solve(const bsr_matrix* A, spand_factor_t M, const do
   using namespace spand;
   const int v = gmres_validate(A, M, b, x, opts);
   if (v != SPAND_OK) return v;
-  const int s = opts->s, m = opts->restart;
   const int64_t N = (int64_t)A->K * A->B;
-  const GmresSizes zs = gmres_sizes(m, s);
-  GmresScratch sc{};
-  auto release = [&] {
-    for (void* p : {(void*)sc.small, (void*)sc.vec, (void*)sc.part, (void*)sc.stat, (void*)sc.dZ, (void*)sc.dY})
-      if (p) cudaFreeAsync(p, st);
-  };
-  if (cudaMallocAsync(&sc.small, zs.small_tot * sizeof(double), st) != cudaSuccess ||
-      cudaMallocAsync(&sc.vec, zs.nvec * N * sizeof(double), st) != cudaSuccess ||
-      cudaMallocAsync(&sc.part, zs.part * sizeof(double), st) != cudaSuccess ||
-      cudaMallocAsync(&sc.stat, 4 * sizeof(int), st) != cudaSuccess ||
-      cudaMallocAsync((void**)&sc.dZ, zs.maxptr * sizeof(double*), st) != cudaSuccess ||
-      cudaMallocAsync((void**)&sc.dY, 64 * sizeof(double*), st) != cudaSuccess) {
-    cudaGetLastError();
-    release();
-    return SPAND_ERR_NOMEM;
+  int status;
+  {
+    OwnedScratch os;
+    status = os.alloc(gmres_sizes(opts->restart, opts->s), N, st);
+    if (status == SPAND_OK) status = sstep_core(A, M, b, x, opts, stats, st, os.sc);
   }
-  int status = sstep_core(A, M, b, x, opts, stats, st, sc);
-  release();
+  if (cudaStreamSynchronize(st) != cudaSuccess && status == SPAND_OK) status = SPAND_ERR_CUDA;
+  return status;
+}
+
+extern "C" int gmres_solve(const bsr_matrix* A, spand_factor_t M, const double* b, double* x,
+                           const gmres_opts* opts, gmres_stats* stats, cudaStream_t st) {
+  using namespace spand;
+  if (!opts) return SPAND_ERR_ARG;
+  gmres_opts o1 = *opts;
+  o1.s = 1;                       // Algorithm 1 has no block size
+  const int v = gmres_validate(A, M, b, x, &o1);
+  if (v != SPAND_OK) return v;
+  const int64_t N = (int64_t)A->K * A->B;
+  int status;
+  {
+    OwnedScratch os;
+    status = os.alloc(gmres_sizes(o1.restart, 1), N, st);
+    if (status == SPAND_OK) status = mgs_core(A, M, b, x, &o1, stats, st, os.sc);
+  }
   if (cudaStreamSynchronize(st) != cudaSuccess && status == SPAND_OK) status = SPAND_ERR_CUDA;
   return status;
 }

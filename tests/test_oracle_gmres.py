@@ -20,6 +20,27 @@ def test_gmres_matches_dense_solve():
     assert np.linalg.norm(x - np.linalg.solve(A, b)) / np.linalg.norm(x) < 1e-10
 
 
+def test_gmres_iterate_is_krylov_minimizer():
+    """Algorithm 1 after k steps (x0 = 0, right preconditioning): x_k = M z with z minimising
+    ||b - A M z|| over span{b, (AM) b, ..., (AM)^(k-1) b}, here by brute force: an orthonormal
+    basis of the explicit Krylov matrix and a dense least-squares solve."""
+    A, b = _tiny(n=120, seed=21)
+    M = np.diag(1.0 + 0.3 * np.sin(np.arange(120)))
+    AM = A @ M
+    for k in (1, 3, 7, 12):
+        K = np.empty((120, k))
+        K[:, 0] = b / np.linalg.norm(b)
+        for j in range(1, k):
+            v = AM @ K[:, j - 1]
+            K[:, j] = v / np.linalg.norm(v)
+        Qk, _ = np.linalg.qr(K)
+        y, *_ = np.linalg.lstsq(AM @ Qk, b, rcond=None)
+        x_ref = M @ (Qk @ y)
+        x, st = gmres(lambda v: A @ v, lambda v: M @ v, b, tol=0.0, restart=k, max_iters=k)
+        assert st.iters == k
+        assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) <= 1e-9
+
+
 @pytest.mark.parametrize("basis", ["newton", "monomial"])
 @pytest.mark.parametrize("s", [2, 4, 5])
 def test_sstep_iterates_equal_gmres(basis, s):
