@@ -208,9 +208,12 @@ typedef struct {
   double t_wait_ms;
   /* the host wall time split by phase (summed over levels): [0] level setup
    * and last-level tail, [1] elimination, [2] scaling, [3] RRQR set-up and
-   * launch, [4] wait for the level's ranks, [5] Q_c formation, [6] merge
-   * into the next level (and the root elimination with the final check),
-   * [7] apply programs                                                      */
+   * launch, ending in the read-back of the level's ranks into pageable host
+   * memory, which returns only once the level's queued kernels have run (so
+   * [3] holds most of the time the host waits for the GPU), [4] the stream
+   * synchronization after it, [5] Q_c formation, [6] merge into the next
+   * level (and the root elimination with the final check), [7] apply
+   * programs                                                                */
   double t_host_phase_ms[8];
 } spand_stats;
 int spand_factor_stats(spand_factor_t F, spand_stats* st);
