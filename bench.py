@@ -118,6 +118,16 @@ def peaks():
     return dict(PEAKS_FALLBACK), "fallback"
 
 
+def max_over_ranks(values, dist=None, device="cpu"):
+    """Element-wise max of per-rank values (the slowest rank's times) by one
+    all_reduce; the values themselves when there is no process group."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
 def run_reference(args):
     """CPU oracle arm: full factor + s-step GMRES solves of the same workload."""
     import numpy as np
@@ -477,10 +487,7 @@ def main():
     bo = h_x.numel() * 8
 
     # ---- max over ranks
-    vals = torch.tensor([t_mx, t_64, 1e3 * statistics.mean(e2e)], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
-    t_mx, t_64, t_e2e = vals.tolist()
+    t_mx, t_64, t_e2e = max_over_ranks([t_mx, t_64, 1e3 * statistics.mean(e2e)], dist, dev)
     if rank != 0:
         if dist:
             dist.destroy_process_group()

@@ -1,0 +1,50 @@
+"""The benchmark's N > 1 path on CPU: world_size-2 gloo ranks under torchrun
+(one independent replica per rank, no collective on the data path; one
+max-reduction of the per-rank times), and the reference arm's rank rule."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+pytest.importorskip("torch")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def test_replicas_max_over_ranks_gloo():
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",
+           "--master-addr=127.0.0.1", f"--master-port={_free_port()}",
+           os.path.join(ROOT, "tests", "dist_replica_worker.py")]
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=240, env=env, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1                      # rank 0 alone prints
+    out = json.loads(lines[0])
+    assert out["world"] == 2
+    assert out["max"] == [11.0, 50.0, 15.0]     # element-wise max of both ranks' values
+    assert out["solves_per_s"] == pytest.approx(2 * 1e3 / 11.0)
+
+
+def test_max_over_ranks_single_process():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks([3.0, 1.5]) == [3.0, 1.5]
+
+
+def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--gpus", "2"])
+    assert bench.run_reference(bench.parse()) == 0
+    assert capsys.readouterr().out == ""
