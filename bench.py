@@ -1,15 +1,23 @@
 """Benchmark: spaND factor + s-step GMRES solve of the DG Newton-step system.
 
-Workload (default): p=2 modal DG Jacobian of 2D Euler on a seeded 64 x 32
-NACA O-grid (K=2048, N=73,728), eps=1e-3, s=4, restart 60, tol 1e-8.  One
-step = spand_factor + sstep_gmres_solve to a true FP64 relative residual
-<= 1e-8, inputs resident in HBM.  The headline form is the mixed one (FP32 /
-TF32 factor and apply, FP64 SpMV / Gram / CholQR / Hessenberg); the FP64 form
-is timed beside it for the speedup.  The L2 is flushed between timed steps.
+Workload (default, the largest single-GPU configuration): p=3 modal DG Jacobian
+of 2D Euler on a seeded 256 x 128 NACA O-grid (K=32,768, N=2,097,152, blocks
+64 x 64, A = 5.35 GB in FP64), M=0.8 with +-10% perturbations, spaND eps=1e-3,
+s-step GMRES s=8, restart 80, tol 1e-8.  One step = spand_factor +
+sstep_gmres_solve to a true FP64 relative residual <= 1e-8, inputs resident in
+HBM (A and the factors are larger than the L2; the L2 is also flushed between
+timed steps).  The headline form is the mixed one (FP32 / TF32 factor and
+apply, FP64 SpMV / Gram / CholQR / Hessenberg); the FP64 form is timed beside it
+for the speedup.  The 64 x 32 p=2 workload (N=73,728) is measured as a
+secondary sub-object (`secondary_C2`), with the pseudo-time continuation and the
+Krylov stress setting.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--config C2|C3|C5]
 
---impl reference times the CPU oracle (NumPy/SciPy) on the same workload.
+--impl reference times the CPU oracle (NumPy/SciPy) on a bounded sample of the
+same workload (a p=3 32 x 16 O-grid with the same flow and solver settings),
+scaled to the full workload by its number of unknowns (spaND factor and solve
+cost grow linearly with N in 2D, Sec. 2.2.1).
 """
 import argparse
 import json
@@ -25,18 +33,18 @@ sys.path.insert(0, ROOT)
 
 METRIC = "spaND factor+s-step GMRES time to 1e-8 rel residual; mixed vs FP64 speedup"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
-# DRAM bytes (read + write) of the RRQR kernels of one C2 mixed factorization,
-# per level, from the ncu capture summarised in profiles/ (null until measured)
-RRQR_TRAFFIC_PER_LEVEL = 63.2e6
+# the oracle sample behind the CPU baseline and the reference arm: the same
+# flow and solver settings on a small grid of the same degree
+CPU_SAMPLE_GRID = (32, 16)
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300")
-    ap.add_argument("--config", default="C2")
+    ap.add_argument("--config", default="C3")
     return ap.parse_args()
 
 
@@ -48,14 +56,38 @@ def workload(cname):
     return c, X, u
 
 
-def config_json(c, extra=None):
-    d = {"workload": f"DG Euler Jacobian p={c.p} O-grid {c.n_theta}x{c.n_r} (K={c.K}, N={c.N}), "
-                     f"spaND eps={c.eps}, s-step GMRES s={c.s} restart={c.restart} tol={c.tol}",
-         "N": c.N, "block": c.B, "eps": c.eps, "s": c.s, "restart": c.restart, "tol": c.tol,
-         "l2": "flushed between timed steps (256 MB write)"}
-    if extra:
-        d.update(extra)
-    return d
+def config_json(c):
+    """The workload as both arms print it (identical dicts)."""
+    return {"workload": f"DG Euler Jacobian p={c.p} O-grid {c.n_theta}x{c.n_r} (K={c.K}, N={c.N}), "
+                        f"M={c.mach}, +-{int(round(100 * c.amp))}% perturbation, spaND eps={c.eps}, "
+                        f"s-step GMRES s={c.s} restart={c.restart} tol={c.tol}",
+            "N": c.N, "block": c.B, "eps": c.eps, "s": c.s, "restart": c.restart, "tol": c.tol,
+            "l2": "inputs larger than L2 when N > 1e6 (A and the factors are GBs); "
+                  "also flushed between timed steps (256 MB write)"}
+
+
+def oracle_sample(c, reps, warm=0):
+    """The oracle (factor + s-step GMRES) on the CPU sample of workload c: the
+    same p, flow and solver settings on a CPU_SAMPLE_GRID O-grid.  Returns
+    (seconds per sample, the sample's N, stats of the last solve)."""
+    from oracle import dg, spand
+    from oracle.gmres import sstep_gmres
+    from synth import modal_state, naca_ogrid
+    nt, nr = CPU_SAMPLE_GRID
+    cs = c.with_(n_theta=min(nt, c.n_theta), n_r=min(nr, c.n_r))
+    X = naca_ogrid(cs.n_theta, cs.n_r, cs.seed)
+    u = modal_state(X, cs.p, cs.mach, cs.alpha_deg, cs.amp, cs.seed)
+    rhs, bsr, _ = dg.assemble(X, cs.p, u, cs.mach, cs.alpha_deg, cs.cfl)
+    A = dg.bsr_to_scipy(*bsr).tocsr()
+    times, st = [], None
+    for k in range(warm + reps):
+        t0 = time.perf_counter()
+        F = spand.factor(bsr, cs.n_theta, cs.n_r, cs.nd_depth, cs.eps)
+        _, st = sstep_gmres(lambda v: A @ v, lambda v: spand.apply(F, v), rhs, s=cs.s, restart=cs.restart,
+                            tol=cs.tol, max_iters=cs.max_iters)
+        if k >= warm:
+            times.append(time.perf_counter() - t0)
+    return times, cs, st
 
 
 class Clocks:
@@ -129,37 +161,29 @@ def max_over_ranks(values, dist=None, device="cpu"):
 
 
 def run_reference(args):
-    """CPU oracle arm: full factor + s-step GMRES solves of the same workload."""
-    import numpy as np
+    """CPU oracle arm: each step is one oracle factor + s-step GMRES solve of the
+    bounded sample (same p, flow and solver settings on a small O-grid),
+    reported in the workload's unit (ms per solve of the full workload) by
+    scaling with the ratio of unknowns; W untimed warm-up samples first."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    from oracle import dg, spand
-    from oracle.gmres import sstep_gmres
-    c, X, u = workload(args.config)
-    rhs, bsr, _ = dg.assemble(X, c.p, u, c.mach, c.alpha_deg, c.cfl)
-    A = dg.bsr_to_scipy(*bsr).tocsr()
-    times = []
-    budget = 180.0
-    t_all = time.time()
-    for k in range(max(1, args.steps)):
-        t0 = time.perf_counter()
-        F = spand.factor(bsr, c.n_theta, c.n_r, c.nd_depth, c.eps)
-        x, st = sstep_gmres(lambda v: A @ v, lambda v: spand.apply(F, v), rhs, s=c.s, restart=c.restart,
-                            tol=c.tol, max_iters=c.max_iters)
-        times.append(time.perf_counter() - t0)
-        if time.time() - t_all > budget:
-            break
-    ms = 1e3 * statistics.mean(times)
+    from synth import get_config
+    c = get_config(args.config)
+    times, cs, st = oracle_sample(c, max(1, args.steps), warm=max(0, args.warmup))
+    scale = c.N / cs.N
+    ms = 1e3 * statistics.mean(times) * scale
     cores = os.cpu_count()
+    sample = (f"oracle factor+solve of a p={cs.p} {cs.n_theta}x{cs.n_r} O-grid (N={cs.N}) with the workload's "
+              f"flow and solver settings, x {scale:.1f} (ratio of unknowns; spaND is O(N) in 2D)")
     out = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus, "steps": len(times),
-           "warmup": 0, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "warmup": max(0, args.warmup), "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
            "config": config_json(c),
-           "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle",
-                            "sample": f"{len(times)} full factor+solve(s) of the workload (oracle as it stands)"},
+           "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-           "true_relres": float(st.true_relres), "iters": st.iters}
+           "sample_s_per_step": statistics.mean(times), "sample_true_relres": float(st.true_relres),
+           "sample_iters": st.iters}
     print(json.dumps(out))
     return 0
 
@@ -277,6 +301,218 @@ def run_batch(args):
     return 0
 
 
+class Workload:
+    """One configuration on the device: seeded grid and state, assembled A and
+    b (device), the ND plan."""
+
+    def __init__(self, sg, torch, dev, name):
+        self.c, X, u = workload(name)
+        self.Xd = torch.as_tensor(X, device=dev)
+        self.ud = torch.as_tensor(u, device=dev)
+        c = self.c
+        self.rhs, self.A, self.dtau = sg.assemble(self.Xd, c.p, self.ud, c.mach, c.alpha_deg, c.cfl)
+        self.plan = sg.Plan(c.n_theta, c.n_r, c.B, c.nd_depth)
+        self.X, self.u = X, u
+
+
+def timed_steps(sg, torch, W, prec, steps, warmup, flush, stream, barrier):
+    """W warm-up then `steps` timed factor + solve steps (CUDA events on the
+    launching stream, L2 flushed before each).  Returns the per-step (factor ms,
+    solve ms), the last step's (factor stats, solve stats, x) and the library's
+    kernel launches in the timed steps."""
+    c = W.c
+
+    def one():
+        F = sg.Factor(W.plan, W.A, c.eps, prec)
+        x, st = sg.sstep_gmres(W.A, F, W.rhs, s=c.s, restart=c.restart, tol=c.tol, max_iters=c.max_iters)
+        return F, x, st
+
+    for _ in range(warmup):
+        F, x, st = one()
+        F.close()
+    ev, last = [], None
+    barrier()
+    n0 = sg.kernel_launches()
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        F = sg.Factor(W.plan, W.A, c.eps, prec)
+        e1.record(stream)
+        x, st = sg.sstep_gmres(W.A, F, W.rhs, s=c.s, restart=c.restart, tol=c.tol, max_iters=c.max_iters)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        ev.append((e0.elapsed_time(e1), e1.elapsed_time(e2)))
+        last = (F.stats(), st, x)
+        F.close()
+    barrier()
+    return ev, last, sg.kernel_launches() - n0
+
+
+def true_relres(sg, torch, W, x):
+    r = sg.spmv(W.A, x)
+    return (torch.linalg.norm(r - W.rhs) / torch.linalg.norm(W.rhs)).item()
+
+
+def rooflines(sg, torch, W, fst, flush, stream, peaks_, sm_count, clk_mhz):
+    """Live rooflines of the kernels of one workload: RRQR (from the last timed
+    factorization's events), elimination GEMMs, the apply sweeps, the block SpMV."""
+    pk, pk_kind = peaks_
+    c = W.c
+    hbm = float(pk.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    # the GEMMs run inside a seconds-long factorization: the sustained bf16 figure
+    bf16 = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"])))
+    tf32_peak = bf16 * (1.1 / 2.25)          # nominal TF32 : BF16 dense ratio
+    # rank-revealing QR of the sparsification; one "launch" = the RRQR phase of
+    # one level (all its kernels between two events on the factor's stream).
+    # The method's work per pivot step k of an n x c interface: E = (n-k)(c-k)
+    # elements, 2E flops for the reflector dot products and 2E for the update
+    # (the library counts 8E bytes: E read + written, FP32).
+    nl = max(1, fst["rrqr_launches"])
+    rr_ms = fst["t_rrqr_ms"] / nl
+    rr_flops = 4.0 * (fst["rrqr_bytes"] / 8.0) / nl
+    rr_ach = rr_flops / (rr_ms * 1e-3) / 1e12 if rr_ms > 0 else 0.0
+    fp32_peak = sm_count * 128 * 2 * clk_mhz * 1e6 / 1e12   # FP32 lanes x 2 flops x SM clock
+    gm_ms = fst["t_elim_gemm_ms"] / max(1, fst["elim_gemm_launches"])
+    gm_fl = fst["elim_gemm_flops"] / max(1, fst["elim_gemm_launches"])
+    gm_ach = gm_fl / (gm_ms * 1e-3) / 1e12 if gm_ms > 0 else 0.0
+    F = sg.Factor(W.plan, W.A, c.eps, "mixed")
+    z = torch.empty_like(W.rhs)
+    for _ in range(3):
+        F.apply(W.rhs, out=z)
+    napp = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(napp):
+        F.apply(W.rhs, out=z)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_apply = e0.elapsed_time(e1) / napp
+    fb = F.stats()["factor_bytes"]
+    F.close()
+    app_ach = fb / (t_apply * 1e-3) / 1e9
+    # block SpMV (FP64): A's blocks and two vectors per launch, L2 flushed before each
+    y = torch.empty_like(W.rhs)
+    sp_ms = []
+    for it in range(13):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sg.spmv(W.A, W.rhs, out=y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if it >= 3:
+            sp_ms.append(e0.elapsed_time(e1))
+    t_spmv = statistics.mean(sp_ms)
+    sp_bytes = W.A.nnzb * W.A.B * W.A.B * 8 + 2 * W.A.K * W.A.B * 8
+    sp_ach = sp_bytes / (t_spmv * 1e-3) / 1e9
+    rr = {"kernel": "k_qrcp_cluster + k_qrcp_group (column-pivoted Householder QR of the interface "
+                    "sparsification; one launch = the RRQR phase of one level)",
+          "bound": "alu", "achieved": rr_ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": rr_ach / fp32_peak,
+          "traffic": None, "peak_kind": f"FP32 lanes x 2 x max SM clock ({sm_count} SMs x 128 x 2 x {clk_mhz:.0f} MHz)",
+          "flops_per_launch": rr_flops, "ms_per_launch": rr_ms,
+          "flops_rule": "4 (n-k)(c-k) per pivot step k: reflector dot products and update"}
+    more = [
+        {"kernel": "k_gemm_umma / k_gemm_tc (elimination Y, X, Schur products; 3xTF32, FP32 accumulation)",
+         "bound": "tensor", "achieved": gm_ach, "peak": tf32_peak, "unit": "TFLOP/s", "frac": gm_ach / tf32_peak,
+         "peak_kind": f"{pk_kind} sustained bf16 x nominal tf32/bf16 ratio (1.1/2.25)", "flops_per_launch": gm_fl,
+         "ms_per_launch": gm_ms},
+        {"kernel": "spand_apply (k_gemv sweeps, FP32 factors)", "bound": "hbm", "achieved": app_ach,
+         "peak": hbm, "unit": "GB/s", "frac": app_ach / hbm, "peak_kind": f"{pk_kind} hbm_gbs",
+         "bytes_per_launch": fb, "ms_per_launch": t_apply},
+        {"kernel": "k_bsr_spmv (FP64 block SpMV, L2 flushed before each launch)", "bound": "hbm",
+         "achieved": sp_ach, "peak": hbm, "unit": "GB/s", "frac": sp_ach / hbm, "peak_kind": f"{pk_kind} hbm_gbs",
+         "bytes_per_launch": sp_bytes, "ms_per_launch": t_spmv}]
+    return rr, more
+
+
+def march_and_stress(sg, torch, W, stream):
+    """The pseudo-time continuation around the step (Eq. 9 CFL ramp, plan reused,
+    A re-assembled and re-factored at every step) and the Krylov stress setting
+    (eps = 1e-1, tolerance 1e-10, at most 100 steps): Algorithm 1 beside
+    Algorithm 2 with their per-phase stream times."""
+    c = W.c
+    mopts = dict(cfl0=c.cfl, cfl_inf=1e6, rtol=0.0, eps=c.eps, precision="mixed", s=c.s, restart=c.restart,
+                 tol=c.tol, max_iters=c.max_iters)
+    try:
+        sg.march(W.Xd, c.p, W.ud, c.mach, c.alpha_deg, W.plan, max_steps=1, **mopts)
+        nm = 5
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        _, hm = sg.march(W.Xd, c.p, W.ud, c.mach, c.alpha_deg, W.plan, max_steps=nm, **mopts)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tm = e0.elapsed_time(e1)
+        march = {"pseudo_time_steps": hm["steps"], "ms": tm, "ms_per_pseudo_time_step": tm / max(1, hm["steps"]),
+                 "per_step": "assemble + ||R|| + spand_factor + s-step GMRES + update (and the final assembly)",
+                 "cfl0": c.cfl, "cfl_inf": 1e6, "res_norm": [float(v) for v in hm["res"]],
+                 "cfl": [float(v) for v in hm["cfl"]], "gmres_iters": [int(v) for v in hm["gmres_iters"]]}
+    except Exception as ex:   # reported, never fatal to the headline line
+        march = {"error": str(ex)}
+    krylov = None
+    try:
+        Fs = sg.Factor(W.plan, W.A, 0.1, "mixed")
+        krylov = {"eps": 0.1, "tol": 1e-10, "max_iters": 100, "restart": 60, "s": c.s, "factor": "mixed"}
+        for name, call in (("gmres_mgs", lambda: sg.gmres(W.A, Fs, W.rhs, restart=60, tol=1e-10, max_iters=100)),
+                           ("sstep_gmres", lambda: sg.sstep_gmres(W.A, Fs, W.rhs, s=c.s, restart=60, tol=1e-10,
+                                                                  max_iters=100))):
+            call()
+            n0 = sg.kernel_launches()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            _, kst = call()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            krylov[name] = {"ms": e0.elapsed_time(e1), "iters": kst["iters"], "converged": kst["converged"],
+                            "true_relres": kst["true_relres"], "reductions": kst["reductions"],
+                            "launches": sg.kernel_launches() - n0,
+                            "phase_ms": {"spmv": kst["t_spmv_ms"], "apply": kst["t_apply_ms"],
+                                         "orth": kst["t_orth_ms"], "other": kst["t_small_ms"]}}
+        Fs.close()
+    except Exception as ex:
+        krylov = {"error": str(ex)}
+    return march, krylov
+
+
+def e2e_steps(sg, torch, W, steps, warmup, flush):
+    """The metric end to end through the public API: every step copies A's values
+    and pattern and b from pinned host memory, factors, solves and reads x back."""
+    c, A = W.c, W.A
+    h_val = A.val.cpu().pin_memory()
+    h_rp = A.row_ptr.cpu().pin_memory()
+    h_col = A.col.cpu().pin_memory()
+    h_b = W.rhs.cpu().pin_memory()
+    h_x = torch.empty_like(h_b).pin_memory()
+    d_val = torch.empty_like(A.val)
+    d_rp = torch.empty_like(A.row_ptr)
+    d_col = torch.empty_like(A.col)
+    d_b = torch.empty_like(W.rhs)
+    A2 = sg.BSR(A.K, A.B, d_rp, d_col, d_val)
+    ts = []
+    for it in range(warmup + steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d_val.copy_(h_val, non_blocking=True)
+        d_rp.copy_(h_rp, non_blocking=True)
+        d_col.copy_(h_col, non_blocking=True)
+        d_b.copy_(h_b, non_blocking=True)
+        F2 = sg.Factor(W.plan, A2, c.eps, "mixed")
+        x2, _ = sg.sstep_gmres(A2, F2, d_b, s=c.s, restart=c.restart, tol=c.tol, max_iters=c.max_iters)
+        h_x.copy_(x2, non_blocking=True)
+        torch.cuda.synchronize()
+        if it >= warmup:
+            ts.append(time.perf_counter() - t0)
+        F2.close()
+    del d_val, h_val
+    bi = A.nnzb * A.B * A.B * 8 + (A.K + 1) * 4 + A.nnzb * 4 + h_b.numel() * 8
+    bo = h_x.numel() * 8
+    return 1e3 * statistics.mean(ts), bi, bo
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -297,257 +533,112 @@ def main():
     import __graft_entry__ as g
     g.build()
     import paper_2101_01763_gb300 as sg
-    c, X, u = workload(args.config)
     stream = torch.cuda.current_stream()
-    Xd = torch.as_tensor(X, device=dev)
-    ud = torch.as_tensor(u, device=dev)
-    rhs, A, dtau = sg.assemble(Xd, c.p, ud, c.mach, c.alpha_deg, c.cfl)
-    plan = sg.Plan(c.n_theta, c.n_r, c.B, c.nd_depth)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
 
     def barrier():
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
 
-    def one(prec):
-        F = sg.Factor(plan, A, c.eps, prec)
-        x, st = sg.sstep_gmres(A, F, rhs, s=c.s, restart=c.restart, tol=c.tol, max_iters=c.max_iters)
-        return F, x, st
-
-    launched = {}
-
-    def timed(prec, steps, warmup):
-        for _ in range(warmup):
-            F, x, st = one(prec)
-            F.close()
-        ev = []
-        stats = None
-        barrier()
-        n0 = sg.kernel_launches()
-        for _ in range(steps):
-            flush.fill_(1.0)
-            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-            e0.record(stream)
-            F = sg.Factor(plan, A, c.eps, prec)
-            e1.record(stream)
-            x, st = sg.sstep_gmres(A, F, rhs, s=c.s, restart=c.restart, tol=c.tol, max_iters=c.max_iters)
-            e2.record(stream)
-            torch.cuda.synchronize()
-            ev.append((e0.elapsed_time(e1), e1.elapsed_time(e2)))
-            stats = (F.stats(), st, x)
-            F.close()
-        barrier()
-        launched[prec] = sg.kernel_launches() - n0
-        return ev, stats
-
-    # ---- headline: mixed form
+    W = Workload(sg, torch, dev, args.config)
+    c = W.c
+    big = c.N > 1_000_000
+    # ---- headline: mixed form, exactly K timed steps after W warm-up steps
     with Clocks(local) as clk:
-        ev_mx, (fst_mx, gst_mx, x_mx) = timed("mixed", args.steps, args.warmup)
-    # ---- FP64 form beside it (fewer steps: its factorization is FP64-ALU bound)
-    k64 = max(2, min(args.steps, 4))
-    ev_64, (fst_64, gst_64, x_64) = timed("fp64", k64, max(1, min(args.warmup, 2)))
-    launches_mx = launched["mixed"]
+        ev_mx, (fst_mx, gst_mx, x_mx), launches_mx = timed_steps(sg, torch, W, "mixed", args.steps, args.warmup,
+                                                                 flush, stream, barrier)
+    relres = true_relres(sg, torch, W, x_mx)
+    # ---- FP64 form beside it (FP64-ALU bound factorization: fewer steps at the large size)
+    k64, w64 = (1, 1) if big else (max(2, min(args.steps, 4)), max(1, min(args.warmup, 2)))
+    ev_64, (fst_64, gst_64, x_64), _ = timed_steps(sg, torch, W, "fp64", k64, w64, flush, stream, barrier)
+    relres64 = true_relres(sg, torch, W, x_64)
     t_mx = statistics.mean(a + b for a, b in ev_mx)
     t_64 = statistics.mean(a + b for a, b in ev_64)
-    # true residual of the final mixed solution (independent FP64 SpMV)
-    r = sg.spmv(A, x_mx)
-    relres = (torch.linalg.norm(r - rhs) / torch.linalg.norm(rhs)).item()
-
-    # ---- rooflines, timed live with CUDA events on the factorization / apply stream
-    pk, pk_kind = peaks()
-    hbm = float(pk.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
-    # the GEMMs run inside a seconds-long factorization: the sustained bf16 figure
-    bf16 = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"])))
-    tf32_peak = bf16 * (1.1 / 2.25)          # nominal TF32 : BF16 dense ratio
-    # dominant kernel of the step: the rank-revealing QR of the sparsification.
-    # One "launch" is the RRQR phase of one level (the cluster, group and
-    # streaming kernels of the level, timed between events on the factor's
-    # stream).  Algorithmic work per pivot step k of an n x c interface:
-    # E = (n-k)(c-k) elements, 2E flops for the dots, 2E for the update, 2E
-    # for the exact norms; the library counts 8E bytes (E read + written).
-    rr_ms = fst_mx["t_rrqr_ms"] / max(1, fst_mx["rrqr_launches"])
-    rr_elems = fst_mx["rrqr_bytes"] / 8.0 / max(1, fst_mx["rrqr_launches"])
-    rr_flops = 6.0 * rr_elems
-    rr_ach = rr_flops / (rr_ms * 1e-3) / 1e12 if rr_ms > 0 else 0.0
-    # FP32 (non-tensor) peak: 152 SMs x 128 FP32 lanes x 2 flops x SM clock
-    clk_mhz = clk.summary().get("sm_max_mhz") or 2070.0
-    fp32_peak = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
-    gm_ms = fst_mx["t_elim_gemm_ms"] / max(1, fst_mx["elim_gemm_launches"])
-    gm_fl = fst_mx["elim_gemm_flops"] / max(1, fst_mx["elim_gemm_launches"])
-    gm_ach = gm_fl / (gm_ms * 1e-3) / 1e12 if gm_ms > 0 else 0.0
-    F = sg.Factor(plan, A, c.eps, "mixed")
-    z = torch.empty_like(rhs)
-    for _ in range(3):
-        F.apply(rhs, out=z)
-    napp = 20
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(napp):
-        F.apply(rhs, out=z)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t_apply = e0.elapsed_time(e1) / napp
-    fb = F.stats()["factor_bytes"]
-    F.close()
-    achieved = fb / (t_apply * 1e-3) / 1e9
-    # block SpMV (FP64): A's blocks and two vectors per launch; the L2 is flushed
-    # before every timed launch (A is smaller than the L2)
-    y = torch.empty_like(rhs)
-    sp_ms = []
-    for it in range(13):
-        flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        sg.spmv(A, rhs, out=y)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        if it >= 3:
-            sp_ms.append(e0.elapsed_time(e1))
-    t_spmv = statistics.mean(sp_ms)
-    sp_bytes = A.nnzb * A.B * A.B * 8 + 2 * A.K * A.B * 8
-    sp_ach = sp_bytes / (t_spmv * 1e-3) / 1e9
-
-    # ---- the pseudo-time continuation around the step (Eq. 9 CFL ramp; the ND plan is
-    # reused and A is re-assembled and re-factored at every step), mixed form
-    mopts = dict(cfl0=c.cfl, cfl_inf=1e6, rtol=0.0, eps=c.eps, precision="mixed", s=c.s, restart=c.restart,
-                 tol=c.tol, max_iters=c.max_iters)
-    try:
-        sg.march(Xd, c.p, ud, c.mach, c.alpha_deg, plan, max_steps=1, **mopts)
-        nm = 5
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        _, hm = sg.march(Xd, c.p, ud, c.mach, c.alpha_deg, plan, max_steps=nm, **mopts)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        tm = e0.elapsed_time(e1)
-        march = {"pseudo_time_steps": hm["steps"], "ms": tm, "ms_per_pseudo_time_step": tm / max(1, hm["steps"]),
-                 "per_step": "assemble + ||R|| + spand_factor + s-step GMRES + update (and the final assembly)",
-                 "cfl0": c.cfl, "cfl_inf": 1e6, "res_norm": [float(v) for v in hm["res"]],
-                 "cfl": [float(v) for v in hm["cfl"]], "gmres_iters": [int(v) for v in hm["gmres_iters"]]}
-    except Exception as ex:   # reported, never fatal to the headline line
-        march = {"error": str(ex)}
-
-    # ---- Krylov stress setting (eps = 1e-1, tolerance 1e-10, at most 100 steps): Algorithm 1
-    # (MGS GMRES) beside Algorithm 2 (s-step), with the solvers' own per-phase stream times
-    krylov = None
-    try:
-        Fs = sg.Factor(plan, A, 0.1, "mixed")
-        krylov = {"eps": 0.1, "tol": 1e-10, "max_iters": 100, "restart": 60, "s": c.s, "factor": "mixed"}
-        for name, call in (("gmres_mgs", lambda: sg.gmres(A, Fs, rhs, restart=60, tol=1e-10, max_iters=100)),
-                           ("sstep_gmres", lambda: sg.sstep_gmres(A, Fs, rhs, s=c.s, restart=60, tol=1e-10,
-                                                                  max_iters=100))):
-            call()
-            n0 = sg.kernel_launches()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            e0.record(stream)
-            _, kst = call()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            krylov[name] = {"ms": e0.elapsed_time(e1), "iters": kst["iters"], "converged": kst["converged"],
-                            "true_relres": kst["true_relres"], "reductions": kst["reductions"],
-                            "launches": sg.kernel_launches() - n0,
-                            "phase_ms": {"spmv": kst["t_spmv_ms"], "apply": kst["t_apply_ms"],
-                                         "orth": kst["t_orth_ms"], "other": kst["t_small_ms"]}}
-        Fs.close()
-    except Exception as ex:
-        krylov = {"error": str(ex)}
-
+    clk_sum = clk.summary()
+    rr, more = rooflines(sg, torch, W, fst_mx, flush, stream, peaks(), sm_count,
+                         clk_sum.get("sm_max_mhz") or 2070.0)
     # ---- end to end through the C ABI with host buffers (pinned), copies inside
-    h_val = A.val.cpu().pin_memory()
-    h_rp = A.row_ptr.cpu().pin_memory()
-    h_col = A.col.cpu().pin_memory()
-    h_b = rhs.cpu().pin_memory()
-    h_x = torch.empty_like(h_b).pin_memory()
-    d_val = torch.empty_like(A.val)
-    d_rp = torch.empty_like(A.row_ptr)
-    d_col = torch.empty_like(A.col)
-    d_b = torch.empty_like(rhs)
-    A2 = sg.BSR(A.K, A.B, d_rp, d_col, d_val)
-    e2e = []
-    for it in range(args.warmup + args.steps):
-        flush.fill_(1.0)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        d_val.copy_(h_val, non_blocking=True)
-        d_rp.copy_(h_rp, non_blocking=True)
-        d_col.copy_(h_col, non_blocking=True)
-        d_b.copy_(h_b, non_blocking=True)
-        F2 = sg.Factor(plan, A2, c.eps, "mixed")
-        x2, _ = sg.sstep_gmres(A2, F2, d_b, s=c.s, restart=c.restart, tol=c.tol, max_iters=c.max_iters)
-        h_x.copy_(x2, non_blocking=True)
-        torch.cuda.synchronize()
-        if it >= args.warmup:
-            e2e.append(time.perf_counter() - t0)
-        F2.close()
-    bi = h_val.numel() * 8 + h_rp.numel() * 4 + h_col.numel() * 4 + h_b.numel() * 8
-    bo = h_x.numel() * 8
+    ke, we = (min(args.steps, 3), 1) if big else (args.steps, args.warmup)
+    t_e2e, bi, bo = e2e_steps(sg, torch, W, ke, we, flush)
+    sec = None
+    if args.config == "C3":
+        # ---- the 64 x 32 p=2 workload as a secondary sub-object
+        W2 = Workload(sg, torch, dev, "C2")
+        k2 = max(3, min(args.steps, 10))
+        ev2, (fst2, gst2, x2), l2 = timed_steps(sg, torch, W2, "mixed", k2, 3, flush, stream, barrier)
+        ev2_64, (_, g2_64, _), _ = timed_steps(sg, torch, W2, "fp64", 3, 1, flush, stream, barrier)
+        rr2, more2 = rooflines(sg, torch, W2, fst2, flush, stream, peaks(), sm_count,
+                               clk_sum.get("sm_max_mhz") or 2070.0)
+        march2, krylov2 = march_and_stress(sg, torch, W2, stream)
+        t2 = statistics.mean(a + b for a, b in ev2)
+        t2_64 = statistics.mean(a + b for a, b in ev2_64)
+        sec = {"config": config_json(W2.c), "ms_per_step_mixed": t2, "ms_per_step_fp64": t2_64,
+               "speedup_mixed_vs_fp64": t2_64 / t2, "steps": k2, "fp64_steps": 3,
+               "factor_ms": statistics.mean(a for a, _ in ev2), "solve_ms": statistics.mean(b for _, b in ev2),
+               "gmres_iters_mixed": gst2["iters"], "gmres_iters_fp64": g2_64["iters"],
+               "reductions_mixed": gst2["reductions"], "true_relres_mixed": true_relres(sg, torch, W2, x2),
+               "gpu_launches_per_step": l2 / k2, "rrqr_ms_per_level": fst2["t_rrqr_level_ms"],
+               "ranks_per_level": fst2["sum_r"], "roofline": rr2, "roofline_more": more2,
+               "pseudo_time_march": march2, "krylov_stress": krylov2}
+        del W2
 
     # ---- max over ranks
-    t_mx, t_64, t_e2e = max_over_ranks([t_mx, t_64, 1e3 * statistics.mean(e2e)], dist, dev)
+    t_mx, t_64, t_e2e = max_over_ranks([t_mx, t_64, t_e2e], dist, dev)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return 0
 
-    # ---- CPU baseline: the oracle on a bounded sample (one full factor+solve)
+    # ---- CPU baseline: the oracle on a bounded sample of the workload, scaled
     cpu = None
     if world == 1 and os.environ.get("BENCH_SKIP_CPU", "0") != "1":
-        from oracle import dg, spand
-        from oracle.gmres import sstep_gmres
-        rhs_o, bsr, _ = dg.assemble(X, c.p, u, c.mach, c.alpha_deg, c.cfl)
-        So = dg.bsr_to_scipy(*bsr).tocsr()
-        t0 = time.perf_counter()
-        Fo = spand.factor(bsr, c.n_theta, c.n_r, c.nd_depth, c.eps)
-        xo, so = sstep_gmres(lambda v: So @ v, lambda v: spand.apply(Fo, v), rhs_o, s=c.s, restart=c.restart,
-                             tol=c.tol, max_iters=c.max_iters)
-        tcpu = time.perf_counter() - t0
-        err = float(np.linalg.norm(x_mx.cpu().numpy() - xo) / np.linalg.norm(xo))
-        cpu = {"value": 1e3 * tcpu, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": "one full factor+solve of the workload (NumPy/SciPy FP64, multithreaded BLAS)",
-               "mixed_solution_rel_err_vs_oracle": err}
+        times, cs, st = oracle_sample(c, 3 if big else 1)
+        scale = c.N / cs.N
+        cpu = {"value": 1e3 * statistics.mean(times) * scale, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{len(times)} oracle factor+solve(s) of a p={cs.p} {cs.n_theta}x{cs.n_r} O-grid "
+                         f"(N={cs.N}) with the workload's flow and solver settings, mean x {scale:.1f} "
+                         f"(ratio of unknowns; spaND is O(N) in 2D)",
+               "sample_s": statistics.mean(times), "sample_true_relres": float(st.true_relres)}
+        if not big:
+            from oracle import dg, spand
+            from oracle.gmres import sstep_gmres
+            rhs_o, bsr, _ = dg.assemble(W.X, c.p, W.u, c.mach, c.alpha_deg, c.cfl)
+            So = dg.bsr_to_scipy(*bsr).tocsr()
+            Fo = spand.factor(bsr, c.n_theta, c.n_r, c.nd_depth, c.eps)
+            xo, _ = sstep_gmres(lambda v: So @ v, lambda v: spand.apply(Fo, v), rhs_o, s=c.s, restart=c.restart,
+                                tol=c.tol, max_iters=c.max_iters)
+            cpu["mixed_solution_rel_err_vs_oracle"] = float(np.linalg.norm(x_mx.cpu().numpy() - xo)
+                                                            / np.linalg.norm(xo))
     out = {
         "metric": METRIC, "value": t_mx, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_mx, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": config_json(c, {"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                                  "form": "mixed (FP32/TF32 factor+apply, FP64 outer)"}),
-        "fp64_ms_per_step": t_64, "speedup_mixed_vs_fp64": t_64 / t_mx,
+        "config": config_json(c),
+        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+        "form": "mixed (FP32/TF32 factor+apply, FP64 outer)",
+        "fp64_ms_per_step": t_64, "fp64_steps": k64, "fp64_warmup": w64, "speedup_mixed_vs_fp64": t_64 / t_mx,
         "factor_ms": statistics.mean(a for a, _ in ev_mx), "solve_ms": statistics.mean(b for _, b in ev_mx),
         "fp64_factor_ms": statistics.mean(a for a, _ in ev_64), "fp64_solve_ms": statistics.mean(b for _, b in ev_64),
         "gmres_iters_mixed": gst_mx["iters"], "gmres_iters_fp64": gst_64["iters"],
+        "reductions_mixed": gst_mx["reductions"], "reductions_fp64": gst_64["reductions"],
+        "sstep_blocks_ran": gst_mx["reductions"] > 0,
+        "true_relres_mixed": relres, "true_relres_fp64": relres64,
+        "mixed_vs_fp64_solution_rel_diff": (torch.linalg.norm(x_mx - x_64) / torch.linalg.norm(x_64)).item(),
         "factor_host_ms": fst_mx["t_host_ms"], "factor_gpu_wait_ms": fst_mx["t_wait_ms"],
         "factor_host_phase_ms": fst_mx["t_host_phase_ms"],
         "rrqr_ms_per_level": fst_mx["t_rrqr_level_ms"], "rrqr_forms_per_level": fst_mx["rrqr_form_count"],
-        "true_relres_mixed": relres, "ranks_per_level": fst_mx["sum_r"],
+        "ranks_per_level": fst_mx["sum_r"], "max_rank_per_level": fst_mx["max_r"],
         "solves_per_s": world * 1e3 / t_mx,
-        "e2e": {"value": t_e2e, "unit": "ms", "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
+        "e2e": {"value": t_e2e, "unit": "ms", "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
+                "steps": ke, "warmup": we},
         "gpu_launches": launches_mx,
         "gpu_launches_per_step": launches_mx / max(1, args.steps),
-        "roofline": {"kernel": "k_qrcp_cluster + k_qrcp_group (column-pivoted Householder QR of the interface "
-                               "sparsification; one launch = the RRQR phase of one level)",
-                     "bound": "alu", "achieved": rr_ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": rr_ach / fp32_peak, "traffic": RRQR_TRAFFIC_PER_LEVEL,
-                     "peak_kind": "FP32 lanes x 2 x max SM clock (152 x 128 x 2 x f)",
-                     "flops_per_launch": rr_flops, "ms_per_launch": rr_ms,
-                     "flops_rule": "6 (n-k)(c-k) per pivot step k: dots, update, exact column norms"},
-        "roofline_more": [
-            {"kernel": "k_gemm_umma (elimination Y, X, Schur products; tcgen05 3xTF32, TMEM accumulator)", "bound": "tensor",
-             "achieved": gm_ach, "peak": tf32_peak, "unit": "TFLOP/s", "frac": gm_ach / tf32_peak,
-             "peak_kind": f"{pk_kind} sustained bf16 x nominal tf32/bf16 ratio (1.1/2.25)", "flops_per_launch": gm_fl,
-             "ms_per_launch": gm_ms},
-            {"kernel": "spand_apply (k_gemv sweeps, FP32 factors)", "bound": "hbm", "achieved": achieved,
-             "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "peak_kind": f"{pk_kind} hbm_gbs",
-             "bytes_per_launch": fb, "ms_per_launch": t_apply},
-            {"kernel": "k_bsr_spmv (FP64 block SpMV, L2 flushed before each launch)", "bound": "hbm",
-             "achieved": sp_ach, "peak": hbm, "unit": "GB/s", "frac": sp_ach / hbm, "peak_kind": f"{pk_kind} hbm_gbs",
-             "bytes_per_launch": sp_bytes, "ms_per_launch": t_spmv}],
-        "pseudo_time_march": march,
-        "krylov_stress": krylov,
-        "clocks": clk.summary(),
+        "roofline": rr,
+        "roofline_more": more,
+        "secondary_C2": sec,
+        "clocks": clk_sum,
         "cpu_baseline": cpu,
     }
     print(json.dumps(out))

@@ -37,6 +37,7 @@ class SpandFactor:
         self.ranks = []        # per level: list of (n_s, r) for sparsified interfaces
         self.flops = 0.0
         self.top_size = 0
+        self.spars_log = []    # with record=True: per sparsified interface (level, W, Q, |diag R|, r)
 
 
 def _lu(A):
@@ -60,8 +61,12 @@ def _m_uinv(U, M):
     return sla.solve_triangular(U, M.T, trans="T", lower=False).T
 
 
-def factor(bsr, n_theta, n_r, D, eps, hierarchy=None):
-    """Factor A (block-CSR tuple (row_ptr, col, val[nnzb,B,B])) with tolerance eps."""
+def factor(bsr, n_theta, n_r, D, eps, hierarchy=None, record=False):
+    """Factor A (block-CSR tuple (row_ptr, col, val[nnzb,B,B])) with tolerance eps.
+
+    record=True keeps, for every sparsified interface, the matrix W it was
+    compressed from, its Q, |diag R| and the kept rank (F.spars_log), so that
+    tests can check the truncation against W itself."""
     row_ptr, col, val = bsr
     K = len(row_ptr) - 1
     B = val.shape[1]
@@ -147,6 +152,8 @@ def factor(bsr, n_theta, n_r, D, eps, hierarchy=None):
             Q[s], rank[s] = Qs, r
             F.flops += 2.0 * W.shape[1] * n_s ** 2 - 2.0 / 3.0 * n_s ** 3 if W.shape[1] >= n_s else 0.0
             lvl_ranks.append((n_s, r))
+            if record:
+                F.spars_log.append(dict(level=l, W=W, Q=Qs, dR=dR, r=r))
             F.ops.append(("spars", cl[s].copy(), Qs))
         F.ranks.append(lvl_ranks)
         for (a, b) in list(blocks):

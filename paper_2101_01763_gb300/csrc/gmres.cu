@@ -466,6 +466,7 @@ struct GmresScratch {
   const double** dZ;
   const double** dY;
   bool timed = false;   // phase times by CUDA events (not in the no-allocation entry point)
+  bool direct_apply = false;   // preconditioner launches issued one by one, never through a CUDA graph
 };
 
 // The solve's stream timeline split into phases: mark(p) records an event, and
@@ -636,7 +637,7 @@ int sstep_core(const bsr_matrix* A, spand_factor_t M, const double* b, double* x
   auto applyM = [&](const double* in, double* out) -> int {
     if (!M) return cudaMemcpyAsync(out, in, N * sizeof(double), cudaMemcpyDeviceToDevice, st) == cudaSuccess
                        ? SPAND_OK : SPAND_ERR_CUDA;
-    return factor_apply(M, in, out, tr, st);
+    return factor_apply(M, in, out, tr, st, sc.direct_apply);
   };
   // G = Z^T Y with column pointer lists
   std::vector<const double*> hz, hy;
@@ -1287,6 +1288,9 @@ extern "C" int sstep_gmres_solve_noalloc(const bsr_matrix* A, spand_factor_t M, 
   sc.dZ = reinterpret_cast<const double**>(p);
   p += b_z;
   sc.dY = reinterpret_cast<const double**>(p);
+  // the factor's apply graph is built on its first use, and building it
+  // allocates: here the apply's launches go on the stream one by one
+  sc.direct_apply = true;
   // sstep_core clears the small-matrix and status words it needs zeroed; the
   // vectors and partial sums are always written before they are read.
   return sstep_core(A, M, b, x, opts, stats, st, sc);

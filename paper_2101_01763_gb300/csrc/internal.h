@@ -14,6 +14,9 @@ namespace spand {
 // With SPAND_DEBUG=1 in the environment, a failing CUDA call is reported on
 // stderr with its source location and the runtime's error string.
 void report_cuda_error(cudaError_t e, const char* expr, const char* file, int line);
+// SPAND_DEBUG level from the environment (0 when unset); 2 also prints the
+// shapes, placements, times and ranks of every level's RRQR problems.
+int debug_level();
 
 #define SPAND_CUDA_TRY(call)                                   \
   do {                                                         \

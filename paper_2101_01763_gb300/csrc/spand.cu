@@ -46,11 +46,16 @@ static double now_ms() {
 
 std::atomic<uint64_t> g_kernel_launches{0};
 
-void report_cuda_error(cudaError_t e, const char* expr, const char* file, int line) {
-  static const bool on = [] {
+int debug_level() {
+  static const int lv = [] {
     const char* v = std::getenv("SPAND_DEBUG");
-    return v && v[0] == '1';
+    return v ? std::atoi(v) : 0;
   }();
+  return lv;
+}
+
+void report_cuda_error(cudaError_t e, const char* expr, const char* file, int line) {
+  const bool on = debug_level() >= 1;
   if (on) std::fprintf(stderr, "spand: %s:%d: %s -> %s (%s)\n", file, line, expr, cudaGetErrorName(e),
                        cudaGetErrorString(e));
 }
@@ -645,7 +650,7 @@ struct FactorBase {
   spand_stats stats{};
   std::vector<spand_stats> sys_stats;   // per system of a batched factorization
   DevMem mem;               // persistent device memory
-  virtual int apply(int prog, const double* r, double* z, int transpose, cudaStream_t st) = 0;
+  virtual int apply(int prog, const double* r, double* z, int transpose, cudaStream_t st, bool direct) = 0;
   virtual int prog_size(int prog) const = 0;
   virtual int64_t prog_bytes(int prog) const = 0;
 };
@@ -653,7 +658,8 @@ struct FactorBase {
 template <typename T>
 struct FactorT;
 template <typename T>
-int apply_impl(FactorT<T>* F, Program<T>& pg, const double* r, double* zout, int transpose, cudaStream_t st);
+int apply_impl(FactorT<T>* F, Program<T>& pg, const double* r, double* zout, int transpose, cudaStream_t st,
+               bool direct);
 
 template <typename T>
 struct FactorT : FactorBase {
@@ -663,8 +669,8 @@ struct FactorT : FactorBase {
   T* park_c = nullptr;
   // [0]: every system; [1 + q]: system q alone (batched factorizations)
   std::vector<std::unique_ptr<Program<T>>> progs;
-  int apply(int prog, const double* r, double* zz, int transpose, cudaStream_t st) override {
-    return apply_impl<T>(this, *progs[prog], r, zz, transpose, st);
+  int apply(int prog, const double* r, double* zz, int transpose, cudaStream_t st, bool direct) override {
+    return apply_impl<T>(this, *progs[prog], r, zz, transpose, st, direct);
   }
   int prog_size(int prog) const override { return progs[prog]->N; }
   int64_t prog_bytes(int prog) const override { return progs[prog]->bytes; }
@@ -1332,6 +1338,31 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
         if (tmp.err) return SPAND_ERR_NOMEM;
         SPAND_CUDA_TRY(cudaMemsetAsync(d_gs, 0, sizeof(GroupSync) * q_coop.size(), st));
       }
+      if (debug_level() >= 2) {
+        // shapes of the level's RRQR problems and how they were placed
+        double sn = 0, sc = 0;
+        int mn = 0, mc = 0;
+        for (auto& t : qt) {
+          sn += t.n;
+          sc += t.c;
+          mn = std::max(mn, t.n);
+          mc = std::max(mc, t.c);
+        }
+        std::fprintf(stderr, "spand: level %d RRQR: %zu interfaces, n mean %.0f max %d, c mean %.0f max %d; "
+                             "clusters 1/2/4/8/16: %zu/%zu/%zu/%zu/%zu, groups in smem %d, streamed %d, "
+                             "cooperative launches %zu\n",
+                     l, qt.size(), sn / std::max<size_t>(1, qt.size()), mn, sc / std::max<size_t>(1, qt.size()), mc,
+                     q_cls[0].size(), q_cls[1].size(), q_cls[2].size(), q_cls[3].size(), q_cls[4].size(),
+                     n_group_smem, n_group_stream + (int)q_gl.size(), coop.size());
+        for (size_t li = 0; li < coop.size() && li < 8; ++li) {
+          std::map<int, int> gsz;
+          for (auto& d : coop[li].desc) gsz[d.G] += (d.q == 0);
+          std::fprintf(stderr, "spand:   cooperative launch %zu: %zu CTAs, %s, groups (G x count):", li,
+                       coop[li].desc.size(), coop[li].smem ? "W in smem" : "W streamed");
+          for (auto& kv : gsz) std::fprintf(stderr, " %dx%d", kv.first, kv.second);
+          std::fprintf(stderr, "\n");
+        }
+      }
       qf[0] = (int)(q_cls[0].size() + q_cls[1].size() + q_cls[2].size() + q_cls[3].size());
       qf[1] = (int)q_cls[4].size();
       qf[2] = n_group_smem;
@@ -1429,6 +1460,16 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       return SPAND_ERR_CUDA;                          // a group barrier ran out of time
     }
     S.t_rrqr_level_ms[l] = ev_read(ev_qr[l]);
+    if (debug_level() >= 2 && !qt.empty()) {
+      long long sr = 0;
+      int mr = 0;
+      for (size_t q = 0; q < qt.size(); ++q) {
+        sr += rank[q];
+        mr = std::max(mr, rank[q]);
+      }
+      std::fprintf(stderr, "spand: level %d RRQR %.3f ms, ranks sum %lld mean %.1f max %d\n", l,
+                   S.t_rrqr_level_ms[l], sr, (double)sr / qt.size(), mr);
+    }
     S.t_rrqr_ms += S.t_rrqr_level_ms[l];
     S.t_elim_gemm_ms += ev_read(ev_gm[l]);
     for (size_t q = 0; q < qt.size(); ++q)
@@ -1897,9 +1938,11 @@ static int run_phases(const std::vector<typename ApplyProg<T>::Phase>& ph, cudaS
 // The phase launches of one sweep pair never change for a factor, so they are
 // captured once per direction into a CUDA graph and replayed; the conversions
 // of the caller's r and z stay outside the graph.  When the caller's stream is
-// itself being captured, the phases are launched directly.
+// itself being captured, or when `direct` is set (the caller may not allocate,
+// and building a graph does), the phases are launched directly.
 template <typename T>
-int apply_impl(FactorT<T>* F, Program<T>& pg, const double* r, double* zout, int transpose, cudaStream_t st) {
+int apply_impl(FactorT<T>* F, Program<T>& pg, const double* r, double* zout, int transpose, cudaStream_t st,
+               bool direct) {
   const int N = pg.N;
   T* w = F->w + pg.off;
   const unsigned g = (unsigned)std::max(1, std::min(4096, (N + 255) / 256));
@@ -1910,7 +1953,7 @@ int apply_impl(FactorT<T>* F, Program<T>& pg, const double* r, double* zout, int
   const auto& bwd = transpose ? pg.prog.tbwd : pg.prog.bwd;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   SPAND_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
-  if (cs != cudaStreamCaptureStatusNone) {
+  if (cs != cudaStreamCaptureStatusNone || direct) {
     run_phases<T>(fwd, st);
     run_phases<T>(bwd, st);
   } else {
@@ -1987,8 +2030,8 @@ struct spand_factor_s {
 };
 
 namespace spand {
-int factor_apply(spand_factor_t F, const double* r, double* z, int transpose, cudaStream_t st) {
-  return F->impl->apply(F->prog, r, z, transpose, st);
+int factor_apply(spand_factor_t F, const double* r, double* z, int transpose, cudaStream_t st, bool direct) {
+  return F->impl->apply(F->prog, r, z, transpose, st, direct);
 }
 int factor_size(spand_factor_t F) { return F->impl->prog_size(F->prog); }
 }  // namespace spand
@@ -2089,7 +2132,7 @@ uint64_t spand_kernel_launches(void) { return spand::g_kernel_launches.load(); }
 
 int spand_apply(spand_factor_t F, const double* r, double* z, int transpose, cudaStream_t stream) {
   if (!F || !r || !z || r == z) return SPAND_ERR_ARG;
-  return spand::factor_apply(F, r, z, transpose, stream);
+  return spand::factor_apply(F, r, z, transpose, stream, false);
 }
 
 }  // extern "C"

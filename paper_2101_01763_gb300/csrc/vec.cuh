@@ -15,7 +15,9 @@ int block_update(int64_t N, int s, int ny, const double* Y, int64_t ldy, const d
                  cudaStream_t st);
 int scale_copy(int64_t N, const double* a, double* b, const double* scal, int invert, cudaStream_t st);
 int axpy_dev(int64_t N, const double* coef, double sign, const double* x, double* y, cudaStream_t st);
-int factor_apply(spand_factor_t F, const double* r, double* z, int transpose, cudaStream_t st);
+// direct = true runs the apply's launches one by one on st, never through the
+// factor's CUDA graph (building a graph allocates; see the no-allocation solve)
+int factor_apply(spand_factor_t F, const double* r, double* z, int transpose, cudaStream_t st, bool direct = false);
 int factor_size(spand_factor_t F);
 
 }  // namespace spand
