@@ -953,6 +953,7 @@ struct GroupX {
   T* slot;                   // [2][G][ns] candidate columns of this group (global)
   int ns;
   int par = 0;
+  long poll_limit = 1l << 22;  // polls before a barrier wait gives up (well under a second)
   __device__ int rank() const { return q; }
   __device__ int size() const { return G; }
   __device__ bool sync() {
@@ -970,7 +971,7 @@ struct GroupX {
       } else {
         long it = 0;
         while (*vgen == g) {
-          if (++it > (1l << 22)) {          // well under a second with the back-off below
+          if (++it > poll_limit) {          // bounded: the back-off below keeps this under a second
             atomicOr(err, 16);
             s_ok = 0;
             break;

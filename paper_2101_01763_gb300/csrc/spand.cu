@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "dense.cuh"
+#include "qrcp_stream.cuh"
 #include "gemv.cuh"
 #include "umma.cuh"
 #include "internal.h"
@@ -424,6 +425,144 @@ static void launch_row_perm(DevMem& tmp, const std::vector<const T*>& src, const
   if (tmp.err) return;
   note_launch();
   k_row_perm<T><<<(unsigned)src.size(), 256, 0, st>>>(a, b, c, d, e);
+}
+
+// ------------------------------------------------------------------ streaming RRQR launch
+// SPAND_QR_STREAM=1 sends every interface with neighbours to the streaming
+// kernel (a checking aid: the same factorization by the other code path);
+// SPAND_QR_STREAM=0 never uses it.
+static int stream_forced() {
+  static const int m = [] {
+    const char* v = std::getenv("SPAND_QR_STREAM");
+    if (v && v[0] == '1') return 1;
+    if (v && v[0] == '0') return -1;
+    return 0;
+  }();
+  return m;
+}
+
+// SPAND_FAULT_GROUP_BARRIER=1: the first streaming RRQR launch of the process
+// tells one group that it has one CTA more than is launched and shortens the
+// barrier's poll limit to about a millisecond, so that the group's first
+// barrier wait runs out; the factorization must then return SPAND_ERR_CUDA and
+// leave the context usable.  A test of the bounded wait; one launch only.
+static bool take_barrier_fault() {
+  static const bool on = [] {
+    const char* v = std::getenv("SPAND_FAULT_GROUP_BARRIER");
+    return v && v[0] == '1';
+  }();
+  static std::atomic<int> used{0};
+  return on && used.exchange(1) == 0;
+}
+
+// leading dimension of a column-major W: n rounded up to 16 bytes
+template <typename T>
+static int qrs_ldw(int n) {
+  constexpr int vw = 16 / sizeof(T);
+  return (n + vw - 1) / vw * vw;
+}
+
+// CTAs of the streaming kernel resident at once (one per SM)
+template <typename T>
+static int qrs_capacity() {
+  int dev = 0, nsm = 0, coop = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return coop ? std::min(nsm, QR_GMAX) : 0;
+}
+
+// register-resident rows of a column: 32 lanes x 16 bytes x NV
+template <typename T>
+static int qrs_pick_nv(int nmax) {
+  constexpr int vw = 16 / sizeof(T);
+  for (int nv : {4, 8}) if (nmax <= 32 * vw * nv) return nv;
+  return 16;
+}
+
+// The streaming RRQR of a list of interfaces in one cooperative launch of one
+// CTA per SM: interfaces with more than twice a CTA's fair share of W's
+// elements get a group of CTAs in proportion; the rest form a queue that every
+// CTA drains once its group (if any) is done, largest first.
+template <typename T, int NV>
+static int launch_qrcp_stream_nv(DevMem& tmp, const std::vector<QrStreamTask<T>>& tasks, int* d_flags, T eps,
+                                 cudaStream_t st) {
+  auto kern = k_qrcp_stream<T, NV>;
+  int dev = 0, nsm = 0, per_sm = 0;
+  SPAND_CUDA_TRY(cudaGetDevice(&dev));
+  SPAND_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int cap = std::min(nsm, QR_GMAX);
+  const size_t nt = tasks.size();
+  double wsum = 0;
+  for (auto& u : tasks) wsum += (double)u.n * u.c;
+  const double fair = wsum / cap;
+  std::vector<int> order(nt);
+  for (size_t i = 0; i < nt; ++i) order[i] = (int)i;
+  std::sort(order.begin(), order.end(), [&](int a, int b) {
+    return (double)tasks[a].n * tasks[a].c > (double)tasks[b].n * tasks[b].c;
+  });
+  std::vector<QrGroupDesc> desc;
+  std::vector<int> solo;
+  size_t smem = 0;
+  int used = 0;
+  for (int i : order) {
+    const double w = (double)tasks[i].n * tasks[i].c;
+    int G = 1;
+    if (w > 2.0 * fair) G = (int)std::lround(w / fair);
+    G = std::max(1, std::min({G, QR_GMAX, cap - used, tasks[i].c}));
+    if (G >= 2) {
+      for (int g = 0; g < G; ++g) desc.push_back({i, g, G, 0});
+      used += G;
+    } else {
+      solo.push_back(i);
+      G = 1;
+    }
+    smem = std::max(smem, qrcp_stream_smem<T>(tasks[i].ldw, tasks[i].c, G));
+  }
+  if (set_dyn_smem((const void*)kern, smem) < (long long)smem) return SPAND_ERR_UNSUPPORTED;
+  SPAND_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, QRS_THREADS, smem));
+  if (per_sm < 1) return SPAND_ERR_UNSUPPORTED;
+  QrStreamTask<T>* dt = tmp.upload(tasks);
+  QrGroupDesc* dd = desc.empty() ? nullptr : tmp.upload(desc);
+  int* ds = solo.empty() ? nullptr : tmp.upload(solo);
+  int* queue = tmp.alloc<int>(1);
+  T* pv = tmp.alloc<T>(nt * 2 * QR_GMAX);
+  int* pi = tmp.alloc<int>(nt * 2 * QR_GMAX);
+  GroupSync* gs = tmp.alloc<GroupSync>(nt);
+  if (tmp.err) return SPAND_ERR_NOMEM;
+  SPAND_CUDA_TRY(cudaMemsetAsync(gs, 0, sizeof(GroupSync) * nt, st));
+  SPAND_CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(int), st));
+  int poll_log2 = 22, fault_task = -1;
+  if (take_barrier_fault()) {
+    fault_task = 0;                         // a partner that never arrives
+    poll_log2 = 14;
+  }
+  const int grid = std::max(1, std::min(cap, std::max(used, (int)solo.size() + used)));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid, 1, 1);
+  cfg.blockDim = dim3(QRS_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  note_launch();
+  SPAND_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, (const QrStreamTask<T>*)dt, (const QrGroupDesc*)dd, used,
+                                    (const int*)ds, (int)solo.size(), queue, pv, pi, gs, d_flags, eps, poll_log2,
+                                    fault_task));
+  return SPAND_OK;
+}
+
+template <typename T>
+static int launch_qrcp_stream(DevMem& tmp, const std::vector<QrStreamTask<T>>& tasks, int nv, int* d_flags, T eps,
+                              cudaStream_t st) {
+  if (nv <= 4) return launch_qrcp_stream_nv<T, 4>(tmp, tasks, d_flags, eps, st);
+  if (nv <= 8) return launch_qrcp_stream_nv<T, 8>(tmp, tasks, d_flags, eps, st);
+  return launch_qrcp_stream_nv<T, 16>(tmp, tasks, d_flags, eps, st);
 }
 
 // blocked getrf of every matrix, in place; pivots + permutations
@@ -1102,6 +1241,8 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
     std::vector<QrTask<T>> qt;
     std::vector<int> qcl;
     std::vector<CopyTask<T>> cps;
+    std::map<const T*, int> w2q;                        // W buffer -> index in qt
+    std::vector<std::pair<int, int>> cps_rng;           // per qt entry: its copy tasks [lo, hi)
     int* d_rank = tmp.alloc<int>(std::max<size_t>(Fc.size(), 1));
     int nmax_qr = 0;
     // the reflector arrays of all interfaces in one zeroed allocation (zero
@@ -1126,7 +1267,9 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       QrTask<T> t;
       t.n = n[s];
       t.c = cs;
-      t.W = tmp.alloc<T>((size_t)n[s] * cs);             // row-major n x c
+      // row-major n x c; room for the column-major n x c layout with its
+      // leading dimension padded to 16 bytes (the streaming kernel's form)
+      t.W = tmp.alloc<T>((size_t)qrs_ldw<T>(n[s]) * cs);
       t.V = vall + voff;
       voff += (((size_t)n[s] * std::min(n[s], cs)) + 63) & ~size_t(63);
       t.tau = tmp.alloc<T>(std::min(n[s], cs));
@@ -1135,6 +1278,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       t.rank = d_rank + qt.size();
       // W = [A_sn A_ns^T]; as a column-major c x n array (ld c) it holds W^T
       int off = 0;
+      cps_rng.push_back({(int)cps.size(), (int)cps.size() + 2 * (int)nba[s].size()});
       for (int b : nba[s]) {
         cps.push_back({blk(s, b), t.W + off, n[s], cs, n[b], n[s], 1});
         off += n[b];
@@ -1143,13 +1287,13 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
         cps.push_back({blk(b, s), t.W + off, n[b], cs, n[b], n[s], 0});
         off += n[b];
       }
+      w2q[t.W] = (int)qt.size();
       qt.push_back(t);
       qcl.push_back(s);
       nmax_qr = std::max(nmax_qr, n[s]);
       if (cs >= n[s]) flops += 2.0 * cs * (double)n[s] * n[s] - 2.0 / 3.0 * pow((double)n[s], 3);
     }
     if (tmp.err) return SPAND_ERR_NOMEM;
-    launch_copy(tmp, cps, st);
     std::vector<int> rank(qt.size());
     int qf[4] = {0, 0, 0, 0};
     if (!qt.empty()) {
@@ -1210,7 +1354,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       std::vector<int> cls_of(qt.size(), -1);
       long long ctas = 0;
       for (size_t k = 0; k < qt.size(); ++k) {
-        for (int ci = 0; ci <= top_cls; ++ci)
+        for (int ci = 0; ci <= top_cls && stream_forced() <= 0; ++ci)
           if ((long long)qrcp_smem_bytes<T>(qt[k].n, qt[k].c, csz[ci]) <= limc[ci]) {
             cls_of[k] = ci;
             break;
@@ -1256,6 +1400,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       };
       std::vector<CoopLaunch> coop;
       std::vector<QrTask<T>> q_coop;
+      std::vector<int> q_strm;                     // indices in qt of the interfaces W streams for
       int n_group_smem = 0, n_group_stream = 0;
       if (!q_big.empty()) {
         auto kg = k_qrcp_group<T, true, QR_THREADS>;
@@ -1276,12 +1421,18 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
         const int cap = std::min(QR_GMAX, coop_ok ? per_sm * nsm : 0);
         const int cap_s = std::min(QR_GMAX, coop_ok ? per_sm_s * nsm : 0);
         std::vector<std::pair<int, int>> in_smem, streamed;   // (task index in q_coop, G)
+        // the streaming kernel: one 512-thread CTA per SM in a cooperative launch
+        const bool strm_ok = coop_ok && stream_forced() >= 0 && qrs_capacity<T>() > 0;
         for (auto& t : q_big) {
           int G = 2;
           while (G <= cap && (long long)qrcp_smem_bytes<T>(t.n, t.c, G) > limg) ++G;
-          if (G <= cap && limg > 0) {
+          if (strm_ok && stream_forced() > 0) {
+            q_strm.push_back(w2q.at(t.W));
+          } else if (G <= cap && limg > 0) {
             in_smem.push_back({(int)q_coop.size(), G});
             q_coop.push_back(t);
+          } else if (strm_ok) {
+            q_strm.push_back(w2q.at(t.W));     // W streams from L2 / HBM (k_qrcp_stream)
           } else if (cap_s >= 16) {
             // about 1 MB of W per CTA, at least 16 CTAs, at most the resident capacity
             const double mb = (double)t.n * t.c * sizeof(T) / (1 << 20);
@@ -1366,7 +1517,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       qf[0] = (int)(q_cls[0].size() + q_cls[1].size() + q_cls[2].size() + q_cls[3].size());
       qf[1] = (int)q_cls[4].size();
       qf[2] = n_group_smem;
-      qf[3] = n_group_stream + (int)q_gl.size();
+      qf[3] = n_group_stream + (int)q_gl.size() + (int)q_strm.size();
       // task arrays are uploaded on st before the fork, so the side stream
       // never reads them ahead of their copies
       QrTask<T>* d_gl = q_gl.empty() ? nullptr : tmp.upload(q_gl);
@@ -1394,6 +1545,51 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
         SPAND_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, dq, (T)eps));
         return SPAND_OK;
       };
+      // W of every interface: row-major for the on-chip forms, column-major
+      // (leading dimension padded to 16 bytes, padding rows zero) for the
+      // streaming kernel
+      std::vector<QrStreamTask<T>> strm;
+      unsigned long long* d_work = nullptr;
+      int strm_nv = 0;
+      {
+        std::vector<char> is_strm(qt.size(), 0);
+        for (int qi : q_strm) is_strm[qi] = 1;
+        if (!q_strm.empty()) {
+          d_work = tmp.alloc<unsigned long long>(q_strm.size());
+          if (tmp.err) return SPAND_ERR_NOMEM;
+          SPAND_CUDA_TRY(cudaMemsetAsync(d_work, 0, sizeof(unsigned long long) * q_strm.size(), st));
+        }
+        std::vector<CopyTask<T>> cps2;
+        cps2.reserve(cps.size());
+        for (size_t qi = 0; qi < qt.size(); ++qi) {
+          const auto rg = cps_rng[qi];
+          if (!is_strm[qi]) {
+            for (int e = rg.first; e < rg.second; ++e) cps2.push_back(cps[e]);
+            continue;
+          }
+          const QrTask<T>& t = qt[qi];
+          const int ldw = qrs_ldw<T>(t.n);
+          if (ldw > t.n) SPAND_CUDA_TRY(cudaMemsetAsync(t.W, 0, sizeof(T) * (size_t)ldw * t.c, st));
+          for (int e = rg.first; e < rg.second; ++e) {
+            const CopyTask<T>& o = cps[e];
+            const size_t off = (size_t)(o.dst - t.W);          // first column of the block in W
+            cps2.push_back({o.src, t.W + off * ldw, o.lds, ldw, o.cols, o.rows, 1 - o.trans});
+          }
+          QrStreamTask<T> u;
+          u.W = t.W;
+          u.V = t.V;
+          u.tau = t.tau;
+          u.Q = nullptr;
+          u.n = t.n;
+          u.c = t.c;
+          u.ldw = ldw;
+          u.rank = t.rank;
+          u.work = d_work + strm.size();
+          strm.push_back(u);
+        }
+        launch_copy(tmp, cps2, st);
+        for (auto& u : strm) strm_nv = std::max(strm_nv, u.n);
+      }
       ev_begin(ev_qr[l]);
       // the streaming launch and the on-chip launches (one stream per cluster size) overlap
       SPAND_CUDA_TRY(cudaEventRecord(sides.fork, st));
@@ -1443,6 +1639,10 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
             SPAND_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_qrcp_group<T, false, 1024>, a0, a1, d_prop_v, d_prop_i, d_gs,
                                               d_flags, d_slots, slot_ns, (T)eps));
         }
+      }
+      if (!strm.empty()) {
+        const int nv = qrs_pick_nv<T>(strm_nv);
+        SPAND_TRY(launch_qrcp_stream<T>(tmp, strm, nv, d_flags, (T)eps, st));
       }
       ev_end(ev_qr[l]);
       S.rrqr_launches += 1;

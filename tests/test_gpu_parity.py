@@ -273,3 +273,107 @@ def test_c2_full_size_properties(sg, prec):
     xr = spla.spsolve(S.tocsc(), rhs_o)
     assert np.linalg.norm(x - xr) / np.linalg.norm(xr) <= 1e-6
 
+
+
+_FORCED_STREAM_CHILD = r"""
+import sys, json
+import numpy as np, torch
+sys.path.insert(0, {root!r})
+import paper_2101_01763_gb300 as sg
+from oracle import dg, spand
+from synth import get_config, modal_state, naca_ogrid
+out = []
+for name in ("C1", "C2"):
+    c = get_config(name)
+    X = naca_ogrid(c.n_theta, c.n_r, c.seed)
+    u = modal_state(X, c.p, c.mach, c.alpha_deg, c.amp, c.seed)
+    rhs_o, bsr, _ = dg.assemble(X, c.p, u, c.mach, c.alpha_deg, c.cfl)
+    A = sg.BSR.from_host(*bsr)
+    F = sg.Factor(sg.Plan(c.n_theta, c.n_r, c.B, c.nd_depth), A, c.eps, "fp64")
+    Fo = spand.factor(bsr, c.n_theta, c.n_r, c.nd_depth, c.eps)
+    st = F.stats()
+    z = F.apply(torch.as_tensor(rhs_o, device="cuda")).cpu().numpy()
+    zo = spand.apply(Fo, rhs_o)
+    Fm = sg.Factor(sg.Plan(c.n_theta, c.n_r, c.B, c.nd_depth), A, c.eps, "mixed")
+    x, gst = sg.sstep_gmres(A, Fm, torch.as_tensor(rhs_o, device="cuda"), s=c.s, restart=c.restart, tol=c.tol)
+    S = dg.bsr_to_scipy(*bsr).tocsr()
+    xr = x.cpu().numpy()
+    out.append(dict(name=name, forms=st["rrqr_form_count"], sum_r=st["sum_r"][:len(Fo.ranks)],
+                    oracle_r=[sum(r for _, r in lv) for lv in Fo.ranks],
+                    apply_err=float(np.linalg.norm(z - zo) / np.linalg.norm(zo)),
+                    mixed_relres=float(np.linalg.norm(S @ xr - rhs_o) / np.linalg.norm(rhs_o)),
+                    converged=bool(gst["converged"])))
+print("RESULT" + json.dumps(out))
+"""
+
+
+def test_streaming_rrqr_matches_oracle(sg):
+    """The streaming RRQR kernel (the form used for interfaces too large for
+    on-chip memory) on every interface of C1 and C2 (SPAND_QR_STREAM=1 in a
+    child process): FP64 ranks equal to the oracle's level by level, the apply
+    equal element by element (1e-9), and the mixed solve converged to 1e-8."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, SPAND_QR_STREAM="1")
+    r = subprocess.run([sys.executable, "-c", _FORCED_STREAM_CHILD.format(root=root)], env=env,
+                       capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stderr[-3000:]
+    res = json.loads(r.stdout.split("RESULT", 1)[1])
+    for d in res:
+        assert all(f[0] == 0 and f[1] == 0 and f[2] == 0 for f in d["forms"]), d   # nothing on-chip
+        assert any(f[3] > 0 for f in d["forms"]), d
+        assert d["sum_r"] == d["oracle_r"], d
+        assert d["apply_err"] <= 1e-9, d
+        assert d["converged"] and d["mixed_relres"] <= 1e-8, d
+
+
+_BARRIER_TIMEOUT_CHILD = r"""
+import sys, json
+import numpy as np, torch
+sys.path.insert(0, {root!r})
+import paper_2101_01763_gb300 as sg
+from oracle import dg, spand
+from synth import get_config, modal_state, naca_ogrid
+c = get_config("C1")
+X = naca_ogrid(c.n_theta, c.n_r, c.seed)
+u = modal_state(X, c.p, c.mach, c.alpha_deg, c.amp, c.seed)
+rhs_o, bsr, _ = dg.assemble(X, c.p, u, c.mach, c.alpha_deg, c.cfl)
+A = sg.BSR.from_host(*bsr)
+plan = sg.Plan(c.n_theta, c.n_r, c.B, c.nd_depth)
+first = None
+try:
+    sg.Factor(plan, A, c.eps, "fp64")
+    first = 0
+except sg.SpandError as e:
+    first = e.status
+F = sg.Factor(plan, A, c.eps, "fp64")          # the same process, after the failed wait
+Fo = spand.factor(bsr, c.n_theta, c.n_r, c.nd_depth, c.eps)
+z = F.apply(torch.as_tensor(rhs_o, device="cuda")).cpu().numpy()
+zo = spand.apply(Fo, rhs_o)
+print("RESULT" + json.dumps(dict(first=first, sum_r=F.stats()["sum_r"][:len(Fo.ranks)],
+                                 oracle_r=[sum(r for _, r in lv) for lv in Fo.ranks],
+                                 apply_err=float(np.linalg.norm(z - zo) / np.linalg.norm(zo)))))
+"""
+
+
+def test_group_barrier_timeout_is_reported(sg):
+    """Failure detection without a GPU fault: the first streaming RRQR launch is
+    told its group has one CTA more than is launched (SPAND_FAULT_GROUP_BARRIER=1,
+    poll limit cut to about ten milliseconds), so the group's barrier wait runs
+    out.  The factorization must return SPAND_ERR_CUDA (-7), and the next
+    factorization in the same process must succeed with the oracle's ranks."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, SPAND_QR_STREAM="1", SPAND_FAULT_GROUP_BARRIER="1")
+    r = subprocess.run([sys.executable, "-c", _BARRIER_TIMEOUT_CHILD.format(root=root)], env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-3000:]
+    d = json.loads(r.stdout.split("RESULT", 1)[1])
+    assert d["first"] == -7, d
+    assert d["sum_r"] == d["oracle_r"] and d["apply_err"] <= 1e-9, d
