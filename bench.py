@@ -354,7 +354,7 @@ def true_relres(sg, torch, W, x):
     return (torch.linalg.norm(r - W.rhs) / torch.linalg.norm(W.rhs)).item()
 
 
-def rooflines(sg, torch, W, fst, flush, stream, peaks_, sm_count, clk_mhz):
+def rooflines(sg, torch, W, fst, flush, stream, peaks_):
     """Live rooflines of the kernels of one workload: RRQR (from the last timed
     factorization's events), elimination GEMMs, the apply sweeps, the block SpMV."""
     pk, pk_kind = peaks_
@@ -363,16 +363,17 @@ def rooflines(sg, torch, W, fst, flush, stream, peaks_, sm_count, clk_mhz):
     # the GEMMs run inside a seconds-long factorization: the sustained bf16 figure
     bf16 = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"])))
     tf32_peak = bf16 * (1.1 / 2.25)          # nominal TF32 : BF16 dense ratio
-    # rank-revealing QR of the sparsification; one "launch" = the RRQR phase of
-    # one level (all its kernels between two events on the factor's stream).
-    # The method's work per pivot step k of an n x c interface: E = (n-k)(c-k)
-    # elements, 2E flops for the reflector dot products and 2E for the update
-    # (the library counts 8E bytes: E read + written, FP32).
+    # rank-revealing QR of the sparsification (k_qrcp_stream); one "launch" = the
+    # RRQR phase of one level (its kernels between two events on the factor's
+    # stream).  Bound by the traffic of the live columns: the kernel counts the
+    # bytes its column passes move (each live column read and written once per
+    # pivot step).  The method's own work, 4 (n-k)(c-k) flops per pivot step
+    # (reflector dot products and update over every column), is reported beside.
     nl = max(1, fst["rrqr_launches"])
     rr_ms = fst["t_rrqr_ms"] / nl
+    rr_bytes = fst["rrqr_stream_bytes"] / nl
+    rr_ach = rr_bytes / (rr_ms * 1e-3) / 1e9 if rr_ms > 0 else 0.0
     rr_flops = 4.0 * (fst["rrqr_bytes"] / 8.0) / nl
-    rr_ach = rr_flops / (rr_ms * 1e-3) / 1e12 if rr_ms > 0 else 0.0
-    fp32_peak = sm_count * 128 * 2 * clk_mhz * 1e6 / 1e12   # FP32 lanes x 2 flops x SM clock
     gm_ms = fst["t_elim_gemm_ms"] / max(1, fst["elim_gemm_launches"])
     gm_fl = fst["elim_gemm_flops"] / max(1, fst["elim_gemm_launches"])
     gm_ach = gm_fl / (gm_ms * 1e-3) / 1e12 if gm_ms > 0 else 0.0
@@ -407,24 +408,54 @@ def rooflines(sg, torch, W, fst, flush, stream, peaks_, sm_count, clk_mhz):
     t_spmv = statistics.mean(sp_ms)
     sp_bytes = W.A.nnzb * W.A.B * W.A.B * 8 + 2 * W.A.K * W.A.B * 8
     sp_ach = sp_bytes / (t_spmv * 1e-3) / 1e9
-    rr = {"kernel": "k_qrcp_cluster + k_qrcp_group (column-pivoted Householder QR of the interface "
-                    "sparsification; one launch = the RRQR phase of one level)",
-          "bound": "alu", "achieved": rr_ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": rr_ach / fp32_peak,
-          "traffic": None, "peak_kind": f"FP32 lanes x 2 x max SM clock ({sm_count} SMs x 128 x 2 x {clk_mhz:.0f} MHz)",
-          "flops_per_launch": rr_flops, "ms_per_launch": rr_ms,
-          "flops_rule": "4 (n-k)(c-k) per pivot step k: reflector dot products and update"}
+    rr = {"kernel": "k_qrcp_stream (column-pivoted Householder QR of the interface sparsification, W streamed "
+                    "from L2/HBM; one launch = the RRQR phase of one level)",
+          "bound": "hbm", "achieved": rr_ach, "peak": hbm, "unit": "GB/s", "frac": rr_ach / hbm, "traffic": None,
+          "peak_kind": f"{pk_kind} hbm_gbs", "bytes_per_launch": rr_bytes, "ms_per_launch": rr_ms,
+          "bytes_rule": "2 (n-k) m_k x 4 per pivot step k, m_k = live columns (counted by the kernel)",
+          "method_flops_per_launch": rr_flops,
+          "method_tflops": rr_flops / (rr_ms * 1e-3) / 1e12 if rr_ms > 0 else 0.0,
+          "method_flops_rule": "4 (n-k)(c-k) per pivot step k over every column"}
+    gm = {"kernel": "k_gemm_umma / k_gemm_tc (elimination Y, X, Schur products; 3xTF32, FP32 accumulation)",
+          "bound": "tensor", "achieved": gm_ach, "peak": tf32_peak, "unit": "TFLOP/s", "frac": gm_ach / tf32_peak,
+          "traffic": None, "peak_kind": f"{pk_kind} sustained bf16 x nominal tf32/bf16 ratio (1.1/2.25)",
+          "flops_per_launch": gm_fl, "ms_per_launch": gm_ms, "flops_rule": "2 m n k per product (logical)"}
     more = [
-        {"kernel": "k_gemm_umma / k_gemm_tc (elimination Y, X, Schur products; 3xTF32, FP32 accumulation)",
-         "bound": "tensor", "achieved": gm_ach, "peak": tf32_peak, "unit": "TFLOP/s", "frac": gm_ach / tf32_peak,
-         "peak_kind": f"{pk_kind} sustained bf16 x nominal tf32/bf16 ratio (1.1/2.25)", "flops_per_launch": gm_fl,
-         "ms_per_launch": gm_ms},
         {"kernel": "spand_apply (k_gemv sweeps, FP32 factors)", "bound": "hbm", "achieved": app_ach,
          "peak": hbm, "unit": "GB/s", "frac": app_ach / hbm, "peak_kind": f"{pk_kind} hbm_gbs",
          "bytes_per_launch": fb, "ms_per_launch": t_apply},
         {"kernel": "k_bsr_spmv (FP64 block SpMV, L2 flushed before each launch)", "bound": "hbm",
          "achieved": sp_ach, "peak": hbm, "unit": "GB/s", "frac": sp_ach / hbm, "peak_kind": f"{pk_kind} hbm_gbs",
          "bytes_per_launch": sp_bytes, "ms_per_launch": t_spmv}]
+    # the headline roofline is the kernel family that takes the most factor time
+    if fst["t_elim_gemm_ms"] >= fst["t_rrqr_ms"]:
+        return gm, [rr] + more
+    return rr, [gm] + more
     return rr, more
+
+
+def gram_rooflines(sg, torch, W, hbm, pk_kind):
+    """The single-reduction kernels of Algorithm 2 at the workload's N, s and
+    restart: one full unpreconditioned s-step cycle (restart columns, so every
+    s-block runs its block Gram reduction and its CGS2 / CholQR2 updates), timed
+    per launch by the solver's own events."""
+    c = W.c
+    kw = dict(s=c.s, restart=c.restart, tol=0.0, max_iters=c.restart)
+    sg.sstep_gmres(W.A, None, W.rhs, **kw)
+    _, st = sg.sstep_gmres(W.A, None, W.rhs, **kw)
+    out = []
+    for name, t, b, n, rule in (
+            ("k_gram_partial + k_gram_reduce (block Gram G = [Q_f, P, V]^T [P, V], FP64)", st["t_gram_ms"],
+             st["gram_bytes"], st["gram_calls"], "(nz + ny) N 8 bytes per reduction"),
+            ("k_block_update (CGS2 / CholQR2 block updates X = Y S^-1 - Z C, FP64)", st["t_bupd_ms"],
+             st["bupd_bytes"], st["bupd_calls"], "(ny + nz + s) N 8 bytes per update")):
+        ms = t / max(1, n)
+        ach = (b / max(1, n)) / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+        out.append({"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                    "frac": ach / hbm, "peak_kind": f"{pk_kind} hbm_gbs", "bytes_per_launch": b / max(1, n),
+                    "ms_per_launch": ms, "launches": n, "bytes_rule": rule,
+                    "setting": f"one unpreconditioned s-step cycle, s={c.s}, restart={c.restart}, N={c.N}"})
+    return out
 
 
 def march_and_stress(sg, torch, W, stream):
@@ -470,7 +501,10 @@ def march_and_stress(sg, torch, W, stream):
                             "true_relres": kst["true_relres"], "reductions": kst["reductions"],
                             "launches": sg.kernel_launches() - n0,
                             "phase_ms": {"spmv": kst["t_spmv_ms"], "apply": kst["t_apply_ms"],
-                                         "orth": kst["t_orth_ms"], "other": kst["t_small_ms"]}}
+                                         "orth": kst["t_orth_ms"], "other": kst["t_small_ms"]},
+                            "gram": {"calls": kst["gram_calls"], "ms": kst["t_gram_ms"], "bytes": kst["gram_bytes"],
+                                     "gbs": kst["gram_bytes"] / (kst["t_gram_ms"] * 1e-3) / 1e9
+                                     if kst["t_gram_ms"] > 0 else None}}
         Fs.close()
     except Exception as ex:
         krylov = {"error": str(ex)}
@@ -535,7 +569,6 @@ def main():
     import paper_2101_01763_gb300 as sg
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
 
     def barrier():
         if dist:
@@ -557,8 +590,9 @@ def main():
     t_mx = statistics.mean(a + b for a, b in ev_mx)
     t_64 = statistics.mean(a + b for a, b in ev_64)
     clk_sum = clk.summary()
-    rr, more = rooflines(sg, torch, W, fst_mx, flush, stream, peaks(), sm_count,
-                         clk_sum.get("sm_max_mhz") or 2070.0)
+    rr, more = rooflines(sg, torch, W, fst_mx, flush, stream, peaks())
+    pk, pk_kind = peaks()
+    more += gram_rooflines(sg, torch, W, float(pk.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"])), pk_kind)
     # ---- end to end through the C ABI with host buffers (pinned), copies inside
     ke, we = (min(args.steps, 3), 1) if big else (args.steps, args.warmup)
     t_e2e, bi, bo = e2e_steps(sg, torch, W, ke, we, flush)
@@ -569,8 +603,7 @@ def main():
         k2 = max(3, min(args.steps, 10))
         ev2, (fst2, gst2, x2), l2 = timed_steps(sg, torch, W2, "mixed", k2, 3, flush, stream, barrier)
         ev2_64, (_, g2_64, _), _ = timed_steps(sg, torch, W2, "fp64", 3, 1, flush, stream, barrier)
-        rr2, more2 = rooflines(sg, torch, W2, fst2, flush, stream, peaks(), sm_count,
-                               clk_sum.get("sm_max_mhz") or 2070.0)
+        rr2, more2 = rooflines(sg, torch, W2, fst2, flush, stream, peaks())
         march2, krylov2 = march_and_stress(sg, torch, W2, stream)
         t2 = statistics.mean(a + b for a, b in ev2)
         t2_64 = statistics.mean(a + b for a, b in ev2_64)

@@ -215,6 +215,11 @@ typedef struct {
    * level (and the root elimination with the final check), [7] apply
    * programs                                                                */
   double t_host_phase_ms[8];
+  /* the streaming RRQR kernel's memory traffic: bytes its column passes moved
+   * (each live column read and written once per pivot step; dead columns are
+   * skipped), in total and per level                                       */
+  double rrqr_stream_bytes;
+  double rrqr_stream_bytes_level[32];
 } spand_stats;
 int spand_factor_stats(spand_factor_t F, spand_stats* st);
 
@@ -266,6 +271,16 @@ typedef struct {
    * Hessenberg, Cholesky, Givens, least squares; host reads of residual
    * estimates; solution update).  Zero in sstep_gmres_solve_noalloc.     */
   double t_spmv_ms, t_apply_ms, t_orth_ms, t_small_ms;
+  /* Kernel times of the block Gram reductions of Algorithm 2 (G = Z^T Y,
+   * Z = [Q_f, P, V], Y = [P, V]) and of the CGS2 / CholQR2 block updates
+   * (X = Y S^-1 - Z C), each with the bytes its launches read and write
+   * (Gram: (nz + ny) N 8 per reduction; update: (ny + nz + s) N 8), CUDA events
+   * around each launch.  Zero in gmres_solve and in
+   * sstep_gmres_solve_noalloc.                                              */
+  double t_gram_ms, gram_bytes;
+  int gram_calls;
+  double t_bupd_ms, bupd_bytes;
+  int bupd_calls;
 } gmres_stats;
 
 int sstep_gmres_solve(const bsr_matrix* A, spand_factor_t M, const double* b, double* x,

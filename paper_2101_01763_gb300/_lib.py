@@ -46,7 +46,8 @@ class SpandStats(C.Structure):
                 ("t_elim_gemm_ms", C.c_double), ("elim_gemm_flops", C.c_double), ("elim_gemm_launches", C.c_int),
                 ("t_rrqr_level_ms", C.c_double * 32), ("rrqr_bytes_level", C.c_double * 32),
                 ("rrqr_form_count", (C.c_int * 4) * 32), ("t_host_ms", C.c_double), ("t_wait_ms", C.c_double),
-                ("t_host_phase_ms", C.c_double * 8)]
+                ("t_host_phase_ms", C.c_double * 8), ("rrqr_stream_bytes", C.c_double),
+                ("rrqr_stream_bytes_level", C.c_double * 32)]
 
 
 class GmresOpts(C.Structure):
@@ -59,7 +60,9 @@ class GmresStats(C.Structure):
                 ("true_relres", C.c_double), ("est_relres", C.c_double), ("orth_err", C.c_double),
                 ("shifts_re", C.c_double * 16), ("shifts_im", C.c_double * 16),
                 ("t_spmv_ms", C.c_double), ("t_apply_ms", C.c_double), ("t_orth_ms", C.c_double),
-                ("t_small_ms", C.c_double)]
+                ("t_small_ms", C.c_double), ("t_gram_ms", C.c_double), ("gram_bytes", C.c_double),
+                ("gram_calls", C.c_int), ("t_bupd_ms", C.c_double), ("bupd_bytes", C.c_double),
+                ("bupd_calls", C.c_int)]
 
 
 class DgMarchOpts(C.Structure):

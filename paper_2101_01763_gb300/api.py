@@ -173,7 +173,9 @@ class Factor:
                     elim_gemm_launches=s.elim_gemm_launches, t_rrqr_level_ms=list(s.t_rrqr_level_ms[:n]),
                     rrqr_bytes_level=list(s.rrqr_bytes_level[:n]),
                     rrqr_form_count=[list(s.rrqr_form_count[l]) for l in range(n)],
-                    t_host_ms=s.t_host_ms, t_wait_ms=s.t_wait_ms, t_host_phase_ms=list(s.t_host_phase_ms))
+                    t_host_ms=s.t_host_ms, t_wait_ms=s.t_wait_ms, t_host_phase_ms=list(s.t_host_phase_ms),
+                    rrqr_stream_bytes=s.rrqr_stream_bytes,
+                    rrqr_stream_bytes_level=list(s.rrqr_stream_bytes_level[:n]))
 
     def close(self):
         if getattr(self, "h", None):
@@ -245,7 +247,9 @@ def _gmres_stats(stt, status):
     return dict(iters=stt.iters, restarts=stt.restarts, reductions=stt.reductions,
                 true_relres=stt.true_relres, est_relres=stt.est_relres, orth_err=stt.orth_err,
                 t_spmv_ms=stt.t_spmv_ms, t_apply_ms=stt.t_apply_ms, t_orth_ms=stt.t_orth_ms,
-                t_small_ms=stt.t_small_ms, converged=(status == L.OK))
+                t_small_ms=stt.t_small_ms, t_gram_ms=stt.t_gram_ms, gram_bytes=stt.gram_bytes,
+                gram_calls=stt.gram_calls, t_bupd_ms=stt.t_bupd_ms, bupd_bytes=stt.bupd_bytes,
+                bupd_calls=stt.bupd_calls, converged=(status == L.OK))
 
 
 def gmres(A, M, b, x0=None, restart=40, tol=1e-8, max_iters=400, transpose=False, stream=None,

@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(256) k_getrf_panel(const MatRef<T>* mats, int 
 // its interchanges move are recorded for k_getrf_swap_trsm, which updates the
 // columns outside the panel.  Used when (n - k0) * 32 values fit the shared
 // budget.
-constexpr int LU_SMEM_BYTES = 160 * 1024;
+constexpr int LU_SMEM_BYTES = 200 * 1024;
 
 template <typename T>
 __global__ void __launch_bounds__(512) k_getrf_panel_smem(const MatRef<T>* mats, int nmat, int k0, int* flags) {

@@ -496,7 +496,51 @@ struct PhaseClock {
     ev.push_back(e);
     ph.push_back(p);
   }
+  // kernel timers of the block Gram reductions (kind 0) and block updates
+  // (kind 1): an event pair around each launch and the bytes it reads/writes
+  struct Kt {
+    cudaEvent_t a, b;
+    int kind;
+    double bytes;
+  };
+  std::vector<Kt> kt;
+  bool kbegin(cudaEvent_t& a) {
+    if (!on) return false;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventRecord(a, st) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return true;
+  }
+  void kend(cudaEvent_t a, int kind, double bytes) {
+    cudaEvent_t b = nullptr;
+    if (cudaEventCreate(&b) != cudaSuccess || cudaEventRecord(b, st) != cudaSuccess) {
+      cudaGetLastError();
+      cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+      return;
+    }
+    kt.push_back({a, b, kind, bytes});
+  }
   void finish(gmres_stats& s) {
+    if (on && !kt.empty() && cudaStreamSynchronize(st) == cudaSuccess) {
+      for (auto& k : kt) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, k.a, k.b) != cudaSuccess) {
+          cudaGetLastError();
+          continue;
+        }
+        if (k.kind == 0) {
+          s.t_gram_ms += ms;
+          s.gram_bytes += k.bytes;
+          s.gram_calls += 1;
+        } else {
+          s.t_bupd_ms += ms;
+          s.bupd_bytes += k.bytes;
+          s.bupd_calls += 1;
+        }
+      }
+    }
     if (on && ev.size() >= 2 && cudaStreamSynchronize(st) == cudaSuccess) {
       double t[4] = {0.0, 0.0, 0.0, 0.0};
       for (size_t i = 0; i + 1 < ev.size(); ++i) {
@@ -515,6 +559,11 @@ struct PhaseClock {
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
     ev.clear();
     ph.clear();
+    for (auto& k : kt) {
+      cudaEventDestroy(k.a);
+      cudaEventDestroy(k.b);
+    }
+    kt.clear();
   }
   ~PhaseClock() { release(); }
 };
@@ -645,7 +694,20 @@ int sstep_core(const bsr_matrix* A, spand_factor_t M, const double* b, double* x
     if (cudaMemcpyAsync(dZ, hz.data(), hz.size() * sizeof(double*), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(dY, hy.data(), hy.size() * sizeof(double*), cudaMemcpyHostToDevice, st) != cudaSuccess)
       return SPAND_ERR_CUDA;
-    return gram(N, (int)hz.size(), dZ, (int)hy.size(), dY, dpart, nblk, G, ldG, st);
+    cudaEvent_t e0 = nullptr;
+    const bool tk = hy.size() >= 2 && clk.kbegin(e0);     // the block Gram reductions of Algorithm 2
+    const int r = gram(N, (int)hz.size(), dZ, (int)hy.size(), dY, dpart, nblk, G, ldG, st);
+    if (tk) clk.kend(e0, 0, (double)(hz.size() + hy.size()) * (double)N * sizeof(double));
+    return r;
+  };
+  // X = Y Sinv + Z C (the block updates of CGS2 + CholQR2), timed like the Gram
+  auto bupd = [&](int ny, const double* Y, const double* Sinv, int nz, const double* Z, const double* Cm, int ldc,
+                  double* X) -> int {
+    cudaEvent_t e0 = nullptr;
+    const bool tk = clk.kbegin(e0);
+    const int r = block_update(N, s, ny, Y, N, Sinv, nz, Z, N, Cm, ldc, X, N, 0, st);
+    if (tk) clk.kend(e0, 1, (double)(ny + nz + s) * (double)N * sizeof(double));
+    return r;
   };
   auto read_scal = [&](int idx, double& v) -> int {
     if (cudaMemcpyAsync(&v, S.scal + idx, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess) return SPAND_ERR_CUDA;
@@ -824,7 +886,7 @@ int sstep_core(const bsr_matrix* A, spand_factor_t M, const double* b, double* x
         if (status) break;
         // Q_P = P S2^-1 - Q_f CP  -> columns c+1..c+s
         clk.mark(PH_ORTH);
-        status = block_update(N, s, s, Pc(0), N, S.S2inv, c + 1, Qc(0), N, S.CP, ldh, Qc(c + 1), N, 0, st);
+        status = bupd(s, Pc(0), S.S2inv, c + 1, Qc(0), S.CP, ldh, Qc(c + 1));
         if (status) break;
         const int c_old = c;
         c += s;
@@ -842,7 +904,7 @@ int sstep_core(const bsr_matrix* A, spand_factor_t M, const double* b, double* x
         }
         // P' = V S1^-1 - Q_{0..c} CV  (into the P slot)
         clk.mark(PH_ORTH);
-        status = block_update(N, s, s, Vc(0), N, S.S1inv, c + 1, Qc(0), N, S.CV, ldh, Pc(0), N, 0, st);
+        status = bupd(s, Vc(0), S.S1inv, c + 1, Qc(0), S.CV, ldh, Pc(0));
         csP = c;
       } else {
         clk.mark(PH_SMALL);
@@ -851,7 +913,7 @@ int sstep_core(const bsr_matrix* A, spand_factor_t M, const double* b, double* x
         status = check_status();
         if (status) break;
         clk.mark(PH_ORTH);
-        status = block_update(N, s, s, Vc(0), N, S.S1inv, c + 1, Qc(0), N, S.CV, ldh, Pc(0), N, 0, st);
+        status = bupd(s, Vc(0), S.S1inv, c + 1, Qc(0), S.CV, ldh, Pc(0));
         csP = c;
         pend = true;
       }
@@ -876,7 +938,7 @@ int sstep_core(const bsr_matrix* A, spand_factor_t M, const double* b, double* x
       status = check_status();
       if (status) break;
       clk.mark(PH_ORTH);
-      status = block_update(N, s, s, Pc(0), N, S.S2inv, c + 1, Qc(0), N, S.CP, ldh, Qc(c + 1), N, 0, st);
+      status = bupd(s, Pc(0), S.S2inv, c + 1, Qc(0), S.CP, ldh, Qc(c + 1));
       if (status) break;
       c += s;
       iters += s;

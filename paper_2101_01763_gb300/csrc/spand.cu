@@ -13,6 +13,7 @@
 // indices), U^-1, X, Y, the scaled triangular inverses and Q_c.  The apply is
 // a fixed list of gather-GEMV launches built once per factorization.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <chrono>
 #include <cstdio>
@@ -30,6 +31,7 @@
 #include "qrcp_stream.cuh"
 #include "gemv.cuh"
 #include "umma.cuh"
+#include "umma2.cuh"
 #include "internal.h"
 
 namespace spand {
@@ -241,10 +243,21 @@ static int gemm_mode() {   // 0: tuned, 1: tcgen05, 2: mma.sync
   static const int m = [] {
     const char* v = std::getenv("SPAND_GEMM");
     if (v && std::strcmp(v, "mma") == 0) return 2;
-    if (v && std::strcmp(v, "umma") == 0) return 1;
+    if (v && (std::strcmp(v, "umma") == 0 || std::strcmp(v, "umma2") == 0)) return 1;
     return 0;
   }();
   return m;
+}
+
+// which tcgen05 kernel: the register-staged 128 x 64 one (default) or the
+// cp.async-pipelined 128 x 128 one (SPAND_GEMM=umma2; measured about 2x slower
+// on the leaf-level elimination products, kept for measurement)
+static bool umma_v1() {
+  static const bool v1 = [] {
+    const char* v = std::getenv("SPAND_GEMM");
+    return !(v && std::strcmp(v, "umma2") == 0);
+  }();
+  return v1;
 }
 
 // Online tuner for the choice of GEMM kernel (and with it the tile shape).
@@ -351,7 +364,8 @@ static void launch_gemm(DevMem& tmp, const std::vector<GemmTask<T>>& tasks, cons
     }
     if (ntask > 0) umma = gemm_pick(chunks / ntask, flops, e0, e1) == 0;
   }
-  const int BM = umma ? UM_BM : 64, BN = umma ? UM_BN : 64;
+  const bool v1 = umma_v1();
+  const int BM = umma ? (v1 ? UM_BM : U2_BM) : 64, BN = umma ? (v1 ? UM_BN : U2_BN) : 64;
   std::vector<TileItem> tiles;
   for (int t = 0; t < (int)tasks.size(); ++t) {
     if (tasks[t].m <= 0 || tasks[t].n <= 0) continue;
@@ -367,10 +381,14 @@ static void launch_gemm(DevMem& tmp, const std::vector<GemmTask<T>>& tasks, cons
   note_launch();
   if constexpr (std::is_same<T, float>::value) {
     if (e0) cudaEventRecord(e0, st);
-    if (umma) {
+    if (umma && v1) {
       static std::atomic<uint64_t> attr{0};
       once_per_device(attr, [] { set_dyn_smem((const void*)k_gemm_umma, UM_SMEM_BYTES); });
       k_gemm_umma<<<(unsigned)tiles.size(), 128, UM_SMEM_BYTES, st>>>(dt, dm, dl);
+    } else if (umma) {
+      static std::atomic<uint64_t> attr2{0};
+      once_per_device(attr2, [] { set_dyn_smem((const void*)k_gemm_umma2, U2_SMEM_BYTES); });
+      k_gemm_umma2<<<(unsigned)tiles.size(), 128, U2_SMEM_BYTES, st>>>(dt, dm, dl);
     } else {
       k_gemm_tc<3><<<(unsigned)tiles.size(), 128, 0, st>>>(dt, dm, dl);   // 3xTF32 on mma.sync
     }
@@ -482,49 +500,30 @@ static int qrs_pick_nv(int nmax) {
   return 16;
 }
 
-// The streaming RRQR of a list of interfaces in one cooperative launch of one
-// CTA per SM: interfaces with more than twice a CTA's fair share of W's
-// elements get a group of CTAs in proportion; the rest form a queue that every
-// CTA drains once its group (if any) is done, largest first.
+// One cooperative launch of the streaming RRQR (one CTA per SM): the groups of
+// desc first, then a queue of single-CTA interfaces drained by every CTA.
 template <typename T, int NV>
-static int launch_qrcp_stream_nv(DevMem& tmp, const std::vector<QrStreamTask<T>>& tasks, int* d_flags, T eps,
-                                 cudaStream_t st) {
+static int launch_stream_once(DevMem& tmp, const QrStreamTask<T>* dt, size_t nt, const std::vector<QrStreamTask<T>>& tasks,
+                              const std::vector<QrGroupDesc>& desc, const std::vector<int>& solo, int* d_flags, T eps,
+                              cudaStream_t st) {
   auto kern = k_qrcp_stream<T, NV>;
   int dev = 0, nsm = 0, per_sm = 0;
   SPAND_CUDA_TRY(cudaGetDevice(&dev));
   SPAND_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const int cap = std::min(nsm, QR_GMAX);
-  const size_t nt = tasks.size();
-  double wsum = 0;
-  for (auto& u : tasks) wsum += (double)u.n * u.c;
-  const double fair = wsum / cap;
-  std::vector<int> order(nt);
-  for (size_t i = 0; i < nt; ++i) order[i] = (int)i;
-  std::sort(order.begin(), order.end(), [&](int a, int b) {
-    return (double)tasks[a].n * tasks[a].c > (double)tasks[b].n * tasks[b].c;
-  });
-  std::vector<QrGroupDesc> desc;
-  std::vector<int> solo;
   size_t smem = 0;
-  int used = 0;
-  for (int i : order) {
-    const double w = (double)tasks[i].n * tasks[i].c;
-    int G = 1;
-    if (w > 2.0 * fair) G = (int)std::lround(w / fair);
-    G = std::max(1, std::min({G, QR_GMAX, cap - used, tasks[i].c}));
-    if (G >= 2) {
-      for (int g = 0; g < G; ++g) desc.push_back({i, g, G, 0});
-      used += G;
-    } else {
-      solo.push_back(i);
-      G = 1;
-    }
-    smem = std::max(smem, qrcp_stream_smem<T>(tasks[i].ldw, tasks[i].c, G));
+  for (size_t d = 0; d < desc.size(); d += desc[d].G)
+    smem = std::max(smem, qrcp_stream_smem<T>(tasks[desc[d].task].ldw, tasks[desc[d].task].c, desc[d].G));
+  for (int i : solo) smem = std::max(smem, qrcp_stream_smem<T>(tasks[i].ldw, tasks[i].c, 1));
+  if (debug_level() >= 2) {
+    std::fprintf(stderr, "spand:   streaming launch: %zu group CTAs (", desc.size());
+    for (size_t d = 0; d < desc.size(); d += desc[d].G)
+      std::fprintf(stderr, " n%d c%d G%d", tasks[desc[d].task].n, tasks[desc[d].task].c, desc[d].G);
+    std::fprintf(stderr, " ), %zu single-CTA interfaces\n", solo.size());
   }
   if (set_dyn_smem((const void*)kern, smem) < (long long)smem) return SPAND_ERR_UNSUPPORTED;
   SPAND_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, QRS_THREADS, smem));
-  if (per_sm < 1) return SPAND_ERR_UNSUPPORTED;
-  QrStreamTask<T>* dt = tmp.upload(tasks);
+  if (per_sm < 1 || (int)desc.size() > cap) return SPAND_ERR_UNSUPPORTED;
   QrGroupDesc* dd = desc.empty() ? nullptr : tmp.upload(desc);
   int* ds = solo.empty() ? nullptr : tmp.upload(solo);
   int* queue = tmp.alloc<int>(1);
@@ -536,10 +535,11 @@ static int launch_qrcp_stream_nv(DevMem& tmp, const std::vector<QrStreamTask<T>>
   SPAND_CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(int), st));
   int poll_log2 = 22, fault_task = -1;
   if (take_barrier_fault()) {
-    fault_task = 0;                         // a partner that never arrives
+    fault_task = desc.empty() ? solo[0] : desc[0].task;   // a partner that never arrives
     poll_log2 = 14;
   }
-  const int grid = std::max(1, std::min(cap, std::max(used, (int)solo.size() + used)));
+  const int used = (int)desc.size();
+  const int grid = std::max(1, std::min(cap, used + (int)solo.size()));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid, 1, 1);
   cfg.blockDim = dim3(QRS_THREADS, 1, 1);
@@ -551,18 +551,70 @@ static int launch_qrcp_stream_nv(DevMem& tmp, const std::vector<QrStreamTask<T>>
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   note_launch();
-  SPAND_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, (const QrStreamTask<T>*)dt, (const QrGroupDesc*)dd, used,
-                                    (const int*)ds, (int)solo.size(), queue, pv, pi, gs, d_flags, eps, poll_log2,
-                                    fault_task));
+  SPAND_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, dt, (const QrGroupDesc*)dd, used, (const int*)ds, (int)solo.size(),
+                                    queue, pv, pi, gs, d_flags, eps, poll_log2, fault_task));
   return SPAND_OK;
 }
 
 template <typename T>
-static int launch_qrcp_stream(DevMem& tmp, const std::vector<QrStreamTask<T>>& tasks, int nv, int* d_flags, T eps,
+static int launch_stream_nv(DevMem& tmp, const QrStreamTask<T>* dt, size_t nt, const std::vector<QrStreamTask<T>>& tasks,
+                            const std::vector<QrGroupDesc>& desc, const std::vector<int>& solo, int* d_flags, T eps,
+                            cudaStream_t st) {
+  int nmax = 0;
+  for (auto& d : desc) nmax = std::max(nmax, tasks[d.task].n);
+  for (int i : solo) nmax = std::max(nmax, tasks[i].n);
+  const int nv = qrs_pick_nv<T>(nmax);
+  if (nv <= 4) return launch_stream_once<T, 4>(tmp, dt, nt, tasks, desc, solo, d_flags, eps, st);
+  if (nv <= 8) return launch_stream_once<T, 8>(tmp, dt, nt, tasks, desc, solo, d_flags, eps, st);
+  return launch_stream_once<T, 16>(tmp, dt, nt, tasks, desc, solo, d_flags, eps, st);
+}
+
+// The streaming RRQR of a level's interfaces.  Interfaces with more than twice
+// a CTA's fair share of the work (estimated as n min(n, c) c: pivot steps x
+// rows x columns) are the critical path: they run first, in groups that
+// share every SM in proportion to their work; then every SM drains a queue of
+// the remaining interfaces one CTA each, largest first.
+template <typename T>
+static int launch_qrcp_stream(DevMem& tmp, const std::vector<QrStreamTask<T>>& tasks, int* d_flags, T eps,
                               cudaStream_t st) {
-  if (nv <= 4) return launch_qrcp_stream_nv<T, 4>(tmp, tasks, d_flags, eps, st);
-  if (nv <= 8) return launch_qrcp_stream_nv<T, 8>(tmp, tasks, d_flags, eps, st);
-  return launch_qrcp_stream_nv<T, 16>(tmp, tasks, d_flags, eps, st);
+  int dev = 0, nsm = 0;
+  SPAND_CUDA_TRY(cudaGetDevice(&dev));
+  SPAND_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int cap = std::min(nsm, QR_GMAX);
+  const size_t nt = tasks.size();
+  auto work = [&](int i) { return (double)tasks[i].n * std::min(tasks[i].n, tasks[i].c) * tasks[i].c; };
+  double wsum = 0;
+  for (size_t i = 0; i < nt; ++i) wsum += work((int)i);
+  const double fair = wsum / cap;
+  std::vector<int> order(nt);
+  for (size_t i = 0; i < nt; ++i) order[i] = (int)i;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
+  std::vector<int> big, solo;
+  for (int i : order) {
+    if (work(i) > 2.0 * fair && tasks[i].c >= 2 && (int)big.size() < cap / 2) big.push_back(i);
+    else solo.push_back(i);
+  }
+  QrStreamTask<T>* dt = tmp.upload(tasks);
+  if (tmp.err) return SPAND_ERR_NOMEM;
+  if (!big.empty()) {
+    // every SM over the large interfaces, in proportion to their work (>= 2 each)
+    double wb = 0;
+    for (int i : big) wb += work(i);
+    std::vector<int> G(big.size(), 2);
+    int left = cap - 2 * (int)big.size();
+    for (size_t b = 0; b < big.size(); ++b) {
+      const int extra = (int)std::floor((cap - 2.0 * big.size()) * work(big[b]) / wb);
+      const int add = std::max(0, std::min({extra, left, QR_GMAX - 2, tasks[big[b]].c - 2}));
+      G[b] += add;
+      left -= add;
+    }
+    std::vector<QrGroupDesc> desc;
+    for (size_t b = 0; b < big.size(); ++b)
+      for (int g = 0; g < G[b]; ++g) desc.push_back({big[b], g, G[b], 0});
+    SPAND_TRY(launch_stream_nv<T>(tmp, dt, nt, tasks, desc, std::vector<int>(), d_flags, eps, st));
+  }
+  if (!solo.empty()) SPAND_TRY(launch_stream_nv<T>(tmp, dt, nt, tasks, std::vector<QrGroupDesc>(), solo, d_flags, eps, st));
+  return SPAND_OK;
 }
 
 // blocked getrf of every matrix, in place; pivots + permutations
@@ -1295,6 +1347,8 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
     }
     if (tmp.err) return SPAND_ERR_NOMEM;
     std::vector<int> rank(qt.size());
+    std::vector<std::array<int, 3>> strm_dbg;     // (n, c, index in qt) of the streamed interfaces (debug)
+    std::vector<unsigned long long> strm_work;   // elements each streamed interface's passes moved
     int qf[4] = {0, 0, 0, 0};
     if (!qt.empty()) {
       // 16-CTA clusters (non-portable size) where the device schedules them
@@ -1351,10 +1405,16 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       limc[3] = set_dyn_smem((const void*)k_qrcp_cluster<T, true, QR_CS, QR_THREADS>, kQrSmemMax);
       limc[4] = cl16 ? set_dyn_smem((const void*)k_qrcp_cluster<T, true, 16, QR_THREADS>, kQrSmemMax) : -1;
       const int top_cls = cl16 ? 4 : 3;
+      // Every interface goes to the streaming kernel when the device runs
+      // cooperative launches: its dropping of dead columns, its balanced column
+      // split and its persistent launches beat the on-chip forms at every level
+      // (same ranks and Q).  The on-chip forms below remain for devices without
+      // cooperative launches and for comparison (SPAND_QR_STREAM=0).
+      const bool all_stream = stream_forced() >= 0 && qrs_capacity<T>() > 0;
       std::vector<int> cls_of(qt.size(), -1);
       long long ctas = 0;
       for (size_t k = 0; k < qt.size(); ++k) {
-        for (int ci = 0; ci <= top_cls && stream_forced() <= 0; ++ci)
+        for (int ci = 0; ci <= top_cls && !all_stream; ++ci)
           if ((long long)qrcp_smem_bytes<T>(qt[k].n, qt[k].c, csz[ci]) <= limc[ci]) {
             cls_of[k] = ci;
             break;
@@ -1426,7 +1486,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
         for (auto& t : q_big) {
           int G = 2;
           while (G <= cap && (long long)qrcp_smem_bytes<T>(t.n, t.c, G) > limg) ++G;
-          if (strm_ok && stream_forced() > 0) {
+          if (strm_ok && all_stream) {
             q_strm.push_back(w2q.at(t.W));
           } else if (G <= cap && limg > 0) {
             in_smem.push_back({(int)q_coop.size(), G});
@@ -1549,8 +1609,8 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       // (leading dimension padded to 16 bytes, padding rows zero) for the
       // streaming kernel
       std::vector<QrStreamTask<T>> strm;
+      std::vector<int> strm_qi;                    // index in qt of each streamed interface
       unsigned long long* d_work = nullptr;
-      int strm_nv = 0;
       {
         std::vector<char> is_strm(qt.size(), 0);
         for (int qi : q_strm) is_strm[qi] = 1;
@@ -1586,9 +1646,10 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
           u.rank = t.rank;
           u.work = d_work + strm.size();
           strm.push_back(u);
+          strm_qi.push_back((int)qi);
         }
         launch_copy(tmp, cps2, st);
-        for (auto& u : strm) strm_nv = std::max(strm_nv, u.n);
+        for (size_t i = 0; i < strm.size(); ++i) strm_dbg.push_back({strm[i].n, strm[i].c, strm_qi[i]});
       }
       ev_begin(ev_qr[l]);
       // the streaming launch and the on-chip launches (one stream per cluster size) overlap
@@ -1640,13 +1701,15 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
                                               d_flags, d_slots, slot_ns, (T)eps));
         }
       }
-      if (!strm.empty()) {
-        const int nv = qrs_pick_nv<T>(strm_nv);
-        SPAND_TRY(launch_qrcp_stream<T>(tmp, strm, nv, d_flags, (T)eps, st));
-      }
+      if (!strm.empty()) SPAND_TRY(launch_qrcp_stream<T>(tmp, strm, d_flags, (T)eps, st));
       ev_end(ev_qr[l]);
       S.rrqr_launches += 1;
       SPAND_CUDA_TRY(cudaMemcpyAsync(rank.data(), d_rank, sizeof(int) * qt.size(), cudaMemcpyDeviceToHost, st));
+      if (!strm.empty()) {
+        strm_work.assign(strm.size(), 0ull);
+        SPAND_CUDA_TRY(cudaMemcpyAsync(strm_work.data(), d_work, sizeof(unsigned long long) * strm.size(),
+                                       cudaMemcpyDeviceToHost, st));
+      }
     }
     mark(3);
     int hflags[4];
@@ -1660,6 +1723,27 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       return SPAND_ERR_CUDA;                          // a group barrier ran out of time
     }
     S.t_rrqr_level_ms[l] = ev_read(ev_qr[l]);
+    for (unsigned long long w : strm_work) S.rrqr_stream_bytes_level[l] += 2.0 * (double)w * sizeof(T);
+    S.rrqr_stream_bytes += S.rrqr_stream_bytes_level[l];
+    if (debug_level() >= 2 && !strm_dbg.empty() && strm_work.size() == strm_dbg.size()) {
+      const std::vector<unsigned long long>& wk = strm_work;
+      {
+        std::vector<int> ord(wk.size());
+        double tot = 0;
+        for (size_t i = 0; i < wk.size(); ++i) {
+          ord[i] = (int)i;
+          tot += (double)wk[i];
+        }
+        std::sort(ord.begin(), ord.end(), [&](int a, int b) { return wk[a] > wk[b]; });
+        std::fprintf(stderr, "spand: level %d streamed %zu interfaces, %.3g elements streamed (%.2f GB read+written)\n",
+                     l, wk.size(), tot, tot * 2 * sizeof(T) / 1e9);
+        for (size_t i = 0; i < std::min<size_t>(6, ord.size()); ++i) {
+          const auto& d = strm_dbg[ord[i]];
+          std::fprintf(stderr, "spand:   n %d c %d rank %d: %.3g elements (%.1f%% of the level)\n", d[0], d[1],
+                       rank[d[2]], (double)wk[ord[i]], 100.0 * wk[ord[i]] / std::max(1.0, tot));
+        }
+      }
+    }
     if (debug_level() >= 2 && !qt.empty()) {
       long long sr = 0;
       int mr = 0;
@@ -2324,6 +2408,8 @@ int spand_factor_stats(spand_factor_t F, spand_stats* st) {
     memcpy(st->t_rrqr_level_ms, B.stats.t_rrqr_level_ms, sizeof(st->t_rrqr_level_ms));
     memcpy(st->rrqr_bytes_level, B.stats.rrqr_bytes_level, sizeof(st->rrqr_bytes_level));
     memcpy(st->rrqr_form_count, B.stats.rrqr_form_count, sizeof(st->rrqr_form_count));
+    st->rrqr_stream_bytes = B.stats.rrqr_stream_bytes;
+    memcpy(st->rrqr_stream_bytes_level, B.stats.rrqr_stream_bytes_level, sizeof(st->rrqr_stream_bytes_level));
   }
   return SPAND_OK;
 }
