@@ -33,6 +33,25 @@ sys.path.insert(0, ROOT)
 
 METRIC = "spaND factor+s-step GMRES time to 1e-8 rel residual; mixed vs FP64 speedup"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+# FP64 arithmetic peak of a GB300 (nominal, the profiling recipe's table: the
+# FP64 rate is a small fraction of the FP32 one on this part).  The FP64 block
+# SpMV, Gram reductions and block updates are bound by it, not by HBM.
+FP64_TFLOPS_NOMINAL = 1.25
+
+
+def dual_bound(entry, flops, hbm_frac):
+    """Add the FP64 arithmetic view of an FP64 kernel and pick as `bound` the
+    roof it is closer to (the binding one)."""
+    ms = entry["ms_per_launch"]
+    tf = flops / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
+    entry["fp64_tflops"] = tf
+    entry["fp64_frac"] = tf / FP64_TFLOPS_NOMINAL
+    entry["fp64_peak_kind"] = "nominal FP64 1.25 TFLOP/s (profiling recipe table)"
+    entry["flops_per_launch"] = flops
+    if entry["fp64_frac"] > hbm_frac:
+        entry.update(bound="alu", achieved=tf, peak=FP64_TFLOPS_NOMINAL, unit="TFLOP/s", frac=entry["fp64_frac"],
+                     peak_kind=entry["fp64_peak_kind"], hbm_frac=hbm_frac)
+    return entry
 # the oracle sample behind the CPU baseline and the reference arm: the same
 # flow and solver settings on a small grid of the same degree
 CPU_SAMPLE_GRID = (32, 16)
@@ -228,23 +247,37 @@ def run_batch(args):
     if cur:
         groups.append(cur)
 
+    grp_ms = [0.0] * len(groups)
+
     def batched():
         xs, st, status = [None] * len(sys_), [None] * len(sys_), [None] * len(sys_)
-        for grp in groups:
+        for gi, grp in enumerate(groups):
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
             Fb = sg.factor_batched([sys_[q][3] for q in grp], [sys_[q][1] for q in grp], c0.eps, "mixed")
             x_g, st_g, s_g = sg.sstep_gmres_batched([sys_[q][1] for q in grp], Fb, [sys_[q][2] for q in grp],
                                                     s=c0.s, restart=c0.restart, tol=c0.tol, max_iters=c0.max_iters)
+            g1.record(stream)
+            torch.cuda.synchronize()
+            grp_ms[gi] = g0.elapsed_time(g1)
             for f in Fb:
                 f.close()
             for k, q in enumerate(grp):
                 xs[q], st[q], status[q] = x_g[k], st_g[k], s_g[k]
         return [], xs, st, status
 
+    sys_ms = {"mixed": [0.0] * len(sys_), "fp64": [0.0] * len(sys_)}
+
     def single(prec):
         out = []
-        for c, A, b, plan in sys_:
+        for q, (c, A, b, plan) in enumerate(sys_):
+            q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            q0.record(stream)
             F = sg.Factor(plan, A, c.eps, prec)
             x, st = sg.sstep_gmres(A, F, b, s=c.s, restart=c.restart, tol=c.tol, max_iters=c.max_iters)
+            q1.record(stream)
+            torch.cuda.synchronize()
+            sys_ms[prec][q] = q0.elapsed_time(q1)
             out.append((x, st))
             F.close()
         return out
@@ -296,7 +329,11 @@ def run_batch(args):
            "ms_per_system_batched": t_b / n, "ms_one_at_a_time_mixed": t_m, "ms_one_at_a_time_fp64": t_64,
            "speedup_vs_one_at_a_time_fp64": t_64 / t_b, "speedup_vs_one_at_a_time_mixed": t_m / t_b,
            "max_true_relres": max(rel), "all_converged": all(v == 0 for v in status),
-           "iters": [s["iters"] for s in st_b], "clocks": clk.summary()}
+           "iters": [s["iters"] for s in st_b], "clocks": clk.summary(),
+           "per_group": [{"systems": len(grp), "N": [cs[q].N for q in grp], "batched_ms": grp_ms[gi],
+                          "one_at_a_time_mixed_ms": sum(sys_ms["mixed"][q] for q in grp),
+                          "one_at_a_time_fp64_ms": sum(sys_ms["fp64"][q] for q in grp)}
+                         for gi, grp in enumerate(groups)]}
     print(json.dumps(out))
     return 0
 
@@ -424,9 +461,10 @@ def rooflines(sg, torch, W, fst, flush, stream, peaks_):
         {"kernel": "spand_apply (k_gemv sweeps, FP32 factors)", "bound": "hbm", "achieved": app_ach,
          "peak": hbm, "unit": "GB/s", "frac": app_ach / hbm, "peak_kind": f"{pk_kind} hbm_gbs",
          "bytes_per_launch": fb, "ms_per_launch": t_apply},
-        {"kernel": "k_bsr_spmv (FP64 block SpMV, L2 flushed before each launch)", "bound": "hbm",
-         "achieved": sp_ach, "peak": hbm, "unit": "GB/s", "frac": sp_ach / hbm, "peak_kind": f"{pk_kind} hbm_gbs",
-         "bytes_per_launch": sp_bytes, "ms_per_launch": t_spmv}]
+        dual_bound({"kernel": "k_bsr_spmv (FP64 block SpMV, L2 flushed before each launch)", "bound": "hbm",
+                    "achieved": sp_ach, "peak": hbm, "unit": "GB/s", "frac": sp_ach / hbm,
+                    "peak_kind": f"{pk_kind} hbm_gbs", "bytes_per_launch": sp_bytes, "ms_per_launch": t_spmv},
+                   2.0 * W.A.nnzb * W.A.B * W.A.B, sp_ach / hbm)]
     # the headline roofline is the kernel family that takes the most factor time
     if fst["t_elim_gemm_ms"] >= fst["t_rrqr_ms"]:
         return gm, [rr] + more
@@ -444,17 +482,29 @@ def gram_rooflines(sg, torch, W, hbm, pk_kind):
     sg.sstep_gmres(W.A, None, W.rhs, **kw)
     _, st = sg.sstep_gmres(W.A, None, W.rhs, **kw)
     out = []
-    for name, t, b, n, rule in (
+    # flops: the Gram G = Z^T Y is 2 nz ny N per reduction; a block update X = Y S^-1 - Z C is
+    # 2 (ny + nz) s N.  The byte counts above fix nz + ny and ny + nz + s per launch, and
+    # ny = 2s (Gram: Y = [P, V]) or s (update), so the flop counts follow from them.
+    s_ = c.s
+    for name, t, b, n, rule, kind in (
             ("k_gram_partial + k_gram_reduce (block Gram G = [Q_f, P, V]^T [P, V], FP64)", st["t_gram_ms"],
-             st["gram_bytes"], st["gram_calls"], "(nz + ny) N 8 bytes per reduction"),
+             st["gram_bytes"], st["gram_calls"], "(nz + ny) N 8 bytes per reduction", 0),
             ("k_block_update (CGS2 / CholQR2 block updates X = Y S^-1 - Z C, FP64)", st["t_bupd_ms"],
-             st["bupd_bytes"], st["bupd_calls"], "(ny + nz + s) N 8 bytes per update")):
+             st["bupd_bytes"], st["bupd_calls"], "(ny + nz + s) N 8 bytes per update", 1)):
         ms = t / max(1, n)
-        ach = (b / max(1, n)) / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
-        out.append({"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                    "frac": ach / hbm, "peak_kind": f"{pk_kind} hbm_gbs", "bytes_per_launch": b / max(1, n),
-                    "ms_per_launch": ms, "launches": n, "bytes_rule": rule,
-                    "setting": f"one unpreconditioned s-step cycle, s={c.s}, restart={c.restart}, N={c.N}"})
+        bl = b / max(1, n)
+        ach = bl / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+        vec = bl / (8.0 * c.N)                 # vectors read per launch
+        if kind == 0:
+            ny = min(2 * s_, vec / 2)
+            fl = 2.0 * (vec - ny) * ny * c.N
+        else:
+            fl = 2.0 * (vec - s_) * s_ * c.N
+        out.append(dual_bound({"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                               "frac": ach / hbm, "peak_kind": f"{pk_kind} hbm_gbs", "bytes_per_launch": bl,
+                               "ms_per_launch": ms, "launches": n, "bytes_rule": rule,
+                               "setting": f"one unpreconditioned s-step cycle, s={c.s}, restart={c.restart}, N={c.N}"},
+                              fl, ach / hbm))
     return out
 
 

@@ -286,6 +286,29 @@ typedef struct {
 int sstep_gmres_solve(const bsr_matrix* A, spand_factor_t M, const double* b, double* x,
                       const gmres_opts* opts, gmres_stats* stats, cudaStream_t stream);
 
+/* sstep_matrix_powers - the matrix-powers step of Algorithm 2 (line 4, Sec.
+ * 2.3) on its own, with the preconditioner fused into the SpMV chain (the
+ * paper applies the s SpMVs with the preconditioner one by one and leaves a
+ * communication-avoiding form to future work).  With V[:, -1] = v0:
+ *   V[:, k] = A M^-1 V[:, k-1] - Re(t_k) V[:, k-1] + [Im(t_k) < 0] Im(t_k)^2 V[:, k-2],
+ * k = 0..s-1 (transpose = 1: A^T M^-T), the Newton basis with conjugate
+ * pairs as real two-steps (the second shift of a pair, Im < 0, follows its
+ * conjugate).  Each step runs the preconditioner's sweeps and then one
+ * shifted block SpMV that reads the preconditioner's own output vector in
+ * place (FP32 in SPAND_MIXED), so M^-1 v is never converted or stored in FP64.
+ * sstep_gmres_solve generates its basis the same way.
+ *  - A, M: as sstep_gmres_solve (M may be NULL: no preconditioner).
+ *  - v0: device FP64 vector of length N = K*B; V: device N x s column-major
+ *    (column k at V + k*N), written; v0 may not lie inside V.
+ *  - shifts_re, shifts_im: host arrays of s doubles (zeros: monomial basis).
+ *  - Not reentrant on one factor (it uses the factor's own vectors).
+ * Errors: SPAND_ERR_ARG (null pointer, s outside 1..64, size mismatch, v0 in
+ * V, a negative-imaginary shift without its conjugate just before it),
+ * SPAND_ERR_CUDA. */
+int sstep_matrix_powers(const bsr_matrix* A, spand_factor_t M, const double* v0, int s,
+                        const double* shifts_re, const double* shifts_im, double* V, int transpose,
+                        cudaStream_t stream);
+
 /* gmres_solve - Algorithm 1: restarted GMRES with modified Gram-Schmidt
  * Arnoldi and Givens rotations, right preconditioning (A M^-1 u = b,
  * x = x0 + M^-1 Q y), the baseline of the s-step solver (Sec. 3.4).  Each

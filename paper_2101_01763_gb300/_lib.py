@@ -97,6 +97,8 @@ EXPORTS = {
                            C.POINTER(GmresStats), C.c_void_p], C.c_int),
     "gmres_solve": ([C.POINTER(BsrMatrix), C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(GmresOpts),
                      C.POINTER(GmresStats), C.c_void_p], C.c_int),
+    "sstep_matrix_powers": ([C.POINTER(BsrMatrix), C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                             C.c_void_p, C.c_int, C.c_void_p], C.c_int),
     "sstep_gmres_solve_batched": ([C.c_int, C.POINTER(BsrMatrix), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                    C.POINTER(C.c_void_p), C.POINTER(GmresOpts), C.POINTER(GmresStats),
                                    C.POINTER(C.c_int), C.c_void_p], C.c_int),

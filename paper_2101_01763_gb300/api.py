@@ -243,6 +243,22 @@ def sstep_gmres(A, M, b, x0=None, s=4, restart=40, tol=1e-8, max_iters=400, basi
     return x, stats
 
 
+def matrix_powers(A, M, v0, shifts, transpose=False, stream=None):
+    """sstep_matrix_powers: the Newton basis [v_1 .. v_s] (N x s device tensor)
+    from v0 with the preconditioner fused into the SpMV chain.  shifts: s
+    complex numbers, conjugate pairs adjacent (+imag first)."""
+    _need(v0, torch.float64, "v0")
+    s = len(shifts)
+    V = torch.empty((s, v0.numel()), dtype=torch.float64, device=v0.device)   # row k = column k of N x s
+    re = (C.c_double * s)(*[complex(t).real for t in shifts])
+    im = (C.c_double * s)(*[complex(t).imag for t in shifts])
+    st = A.struct()
+    L.check(L.lib().sstep_matrix_powers(C.byref(st), M.h if M is not None else None, _ptr(v0), s,
+                                        C.cast(re, C.c_void_p), C.cast(im, C.c_void_p), _ptr(V), int(transpose),
+                                        _stream(stream)), "sstep_matrix_powers")
+    return V.T
+
+
 def _gmres_stats(stt, status):
     return dict(iters=stt.iters, restarts=stt.restarts, reductions=stt.reductions,
                 true_relres=stt.true_relres, est_relres=stt.est_relres, orth_err=stt.orth_err,

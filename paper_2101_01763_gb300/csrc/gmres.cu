@@ -852,13 +852,22 @@ int sstep_core(const bsr_matrix* A, spand_factor_t M, const double* b, double* x
       for (int k = 0; k < s && !status; ++k) {
         const double* vk = (k == 0) ? w0 : Vc(k - 1);
         const double* vkm = (k == 0) ? nullptr : ((k == 1) ? w0 : Vc(k - 2));
-        clk.mark(PH_APPLY);
-        status = applyM(vk, u);
-        if (status) break;
         const std::complex<double> t = shifts[k];
+        const double a2 = t.imag() < 0 ? t.imag() * t.imag() : 0.0;
+        if (!M) {
+          clk.mark(PH_SPMV);
+          status = spmv_fused(A, vk, Vc(k), tr, 1.0, -t.real(), vk, a2, t.imag() < 0 ? vkm : nullptr, st);
+          continue;
+        }
+        // the preconditioner's sweeps leave M^-1 v_k in the factor's own vector
+        // (FP32 in the mixed form), which the shifted SpMV reads in place
+        clk.mark(PH_APPLY);
+        const void* w = nullptr;
+        int wf = 0;
+        status = factor_apply_slot(M, vk, tr, st, sc.direct_apply, &w, &wf);
+        if (status) break;
         clk.mark(PH_SPMV);
-        status = spmv_fused(A, u, Vc(k), tr, 1.0, -t.real(), vk, t.imag() < 0 ? t.imag() * t.imag() : 0.0,
-                            t.imag() < 0 ? vkm : nullptr, st);
+        status = spmv_fused_x(A, w, wf, Vc(k), tr, 1.0, -t.real(), vk, a2, t.imag() < 0 ? vkm : nullptr, st);
       }
       if (status) break;
       // ---- the single reduction
@@ -1359,3 +1368,43 @@ extern "C" int sstep_gmres_solve_noalloc(const bsr_matrix* A, spand_factor_t M, 
 }
 
 extern "C" size_t sstep_gmres_noalloc_capacity(void) { return spand::kNoAllocScratchBytes; }
+
+// ------------------------------------------------------------------ matrix powers
+// The Newton-basis matrix-powers step of Algorithm 2 on its own: with M the
+// preconditioner, V[:, k] = A M^-1 V[:, k-1] - Re(t_k) V[:, k-1]
+// (+ Im(t_k)^2 V[:, k-2] for the second shift of a conjugate pair), V[:, -1] = v0.
+// Each step is the preconditioner's sweeps followed by one shifted block SpMV
+// that reads the preconditioner's output vector in place (FP32 in the mixed
+// form): no conversion pass and no FP64 copy of M^-1 v_k.
+extern "C" int sstep_matrix_powers(const bsr_matrix* A, spand_factor_t M, const double* v0, int s,
+                                   const double* shifts_re, const double* shifts_im, double* V, int transpose,
+                                   cudaStream_t st) {
+  using namespace spand;
+  if (!A || !v0 || !V || !shifts_re || !shifts_im || !A->row_ptr || !A->col || !A->val || s < 1 || s > 64)
+    return SPAND_ERR_ARG;
+  const int64_t N = (int64_t)A->K * A->B;
+  if (M && factor_size(M) != N) return SPAND_ERR_ARG;
+  if (v0 >= V && v0 < V + (size_t)s * N) return SPAND_ERR_ARG;     // v0 may not lie in V
+  for (int k = 0; k < s; ++k)
+    if (shifts_im[k] < 0 && (k == 0 || shifts_im[k - 1] != -shifts_im[k] || shifts_re[k - 1] != shifts_re[k]))
+      return SPAND_ERR_ARG;                                          // a pair's second shift follows its first
+  const int tr = transpose ? 1 : 0;
+  for (int k = 0; k < s; ++k) {
+    const double* vk = (k == 0) ? v0 : V + (size_t)(k - 1) * N;
+    const double* vkm = (k == 0) ? nullptr : ((k == 1) ? v0 : V + (size_t)(k - 2) * N);
+    const double a2 = shifts_im[k] < 0 ? shifts_im[k] * shifts_im[k] : 0.0;
+    double* out = V + (size_t)k * N;
+    int status;
+    if (!M) {
+      status = spmv_fused(A, vk, out, tr, 1.0, -shifts_re[k], vk, a2, shifts_im[k] < 0 ? vkm : nullptr, st);
+    } else {
+      const void* w = nullptr;
+      int wf = 0;
+      status = factor_apply_slot(M, vk, tr, st, false, &w, &wf);
+      if (status == SPAND_OK)
+        status = spmv_fused_x(A, w, wf, out, tr, 1.0, -shifts_re[k], vk, a2, shifts_im[k] < 0 ? vkm : nullptr, st);
+    }
+    if (status != SPAND_OK) return status;
+  }
+  return SPAND_OK;
+}

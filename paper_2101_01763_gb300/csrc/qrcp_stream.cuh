@@ -10,8 +10,10 @@
 // processes one column at a time: it loads rows floor(k)..n-1 into registers
 // with 16-byte loads (NV vectors per lane, all in flight at once), forms the
 // reflector dot product with a shuffle reduction, updates the column in
-// registers, stores it back and recomputes its residual norm exactly.  One
-// read and one write of every live column per pivot step.
+// registers, stores it back and recomputes its residual norm exactly (columns
+// of up to 32 x 16 x NV bytes go 16 / NV at a time, so that a warp always has
+// 16 vector loads per lane in flight).  One read and one write of every live
+// column per pivot step.
 //
 // Columns that can no longer be pivots are dropped for good: the residual norm
 // of a column never grows, and the factorization stops at the first step whose
@@ -152,6 +154,64 @@ __device__ inline T qrs_column(T* __restrict__ col, const T* __restrict__ v, T t
   return warp_sum(s);
 }
 
+// CB columns at once (register path only: n - kb <= 32 NV VW): all their
+// loads are in flight together, so a warp keeps CB x NV 16-byte loads per lane
+// outstanding.  act[b] = false skips column b.  sres[b]: residual norm^2.
+template <typename T, int NV, int CB>
+__device__ inline void qrs_columns(T* const (&col)[CB], const bool (&act)[CB], const T* __restrict__ v, T tau,
+                                   int k, int kb, int n, int lane, T (&sres)[CB]) {
+  using VT = Vec16<T>;
+  constexpr int VW = VT::W;
+  typename VT::V r[CB][NV];
+#pragma unroll
+  for (int b = 0; b < CB; ++b)
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+      const int i0 = kb + (lane + 32 * t) * VW;
+      if (act[b] && i0 < n) r[b][t] = VT::load(col[b] + i0);
+    }
+  T d[CB];
+#pragma unroll
+  for (int b = 0; b < CB; ++b) d[b] = 0;
+#pragma unroll
+  for (int t = 0; t < NV; ++t) {
+    const int i0 = kb + (lane + 32 * t) * VW;
+    if (i0 < n) {
+      const typename VT::V vv = VT::load(v + i0);
+#pragma unroll
+      for (int b = 0; b < CB; ++b)
+        if (act[b])
+#pragma unroll
+          for (int e = 0; e < VW; ++e) d[b] += VT::get(vv, e) * VT::get(r[b][t], e);
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < CB; ++b) d[b] = warp_sum(d[b]) * tau;
+  T sq[CB];
+#pragma unroll
+  for (int b = 0; b < CB; ++b) sq[b] = 0;
+#pragma unroll
+  for (int t = 0; t < NV; ++t) {
+    const int i0 = kb + (lane + 32 * t) * VW;
+    if (i0 < n) {
+      const typename VT::V vv = VT::load(v + i0);
+#pragma unroll
+      for (int b = 0; b < CB; ++b)
+        if (act[b]) {
+#pragma unroll
+          for (int e = 0; e < VW; ++e) {
+            const T a = VT::get(r[b][t], e) - d[b] * VT::get(vv, e);
+            VT::set(r[b][t], e, a);
+            if (i0 + e > k) sq[b] += a * a;
+          }
+          VT::store(col[b] + i0, r[b][t]);
+        }
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < CB; ++b) sres[b] = warp_sum(sq[b]);
+}
+
 // squared norm of rows [kb, n) of a column (kb vector-aligned)
 template <typename T>
 __device__ inline T qrs_norm2(const T* __restrict__ col, int kb, int n, int lane) {
@@ -285,17 +345,43 @@ __device__ bool qrs_task(const QrStreamTask<T>& tk, int q, int G, int Gx, T* pro
     best = -1;
     bi = c;
     int kept = 0;
-    for (int t = 0; t < cnt; ++t) {
-      const int j = list[t];
-      if (j == p) continue;                 // the pivot column is done (warp-uniform)
-      const T s = qrs_column<T, NV>(tk.W + (size_t)j * ldw, v, tau, k, kb, n, lane);
-      __syncwarp();
-      if (s > cut2) {
-        if (lane == 0) list[kept] = j;      // kept <= t: compacted in place, in order
-        ++kept;
-        argmax_pair(best, bi, s, j);
+    constexpr int CB = (NV >= 16) ? 1 : 16 / NV;   // columns in flight per warp on the register path
+    if (CB > 1 && n - kb <= 32 * VW * NV) {
+      for (int t = 0; t < cnt; t += CB) {
+        int js[CB];
+        bool act[CB];
+        T* cols[CB];
+#pragma unroll
+        for (int b = 0; b < CB; ++b) {
+          js[b] = (t + b < cnt) ? list[t + b] : -1;
+          act[b] = js[b] >= 0 && js[b] != p;  // the pivot column is done (warp-uniform)
+          cols[b] = tk.W + (size_t)(act[b] ? js[b] : 0) * ldw;
+        }
+        T sres[CB];
+        qrs_columns<T, NV, CB>(cols, act, v, tau, k, kb, n, lane, sres);
+        __syncwarp();
+#pragma unroll
+        for (int b = 0; b < CB; ++b)
+          if (act[b] && sres[b] > cut2) {
+            if (lane == 0) list[kept] = js[b];   // kept <= t + b: compacted in place, in order
+            ++kept;
+            argmax_pair(best, bi, sres[b], js[b]);
+          }
+        __syncwarp();
       }
-      __syncwarp();
+    } else {
+      for (int t = 0; t < cnt; ++t) {
+        const int j = list[t];
+        if (j == p) continue;                 // the pivot column is done (warp-uniform)
+        const T s = qrs_column<T, NV>(tk.W + (size_t)j * ldw, v, tau, k, kb, n, lane);
+        __syncwarp();
+        if (s > cut2) {
+          if (lane == 0) list[kept] = j;      // kept <= t: compacted in place, in order
+          ++kept;
+          argmax_pair(best, bi, s, j);
+        }
+        __syncwarp();
+      }
     }
     work += (unsigned long long)(n - k) * (unsigned long long)cnt;
     cnt = kept;

@@ -842,6 +842,9 @@ struct FactorBase {
   std::vector<spand_stats> sys_stats;   // per system of a batched factorization
   DevMem mem;               // persistent device memory
   virtual int apply(int prog, const double* r, double* z, int transpose, cudaStream_t st, bool direct) = 0;
+  // sweeps only: the output stays in the factor's own vector (returned)
+  virtual int apply_slot(int prog, const double* r, int transpose, cudaStream_t st, bool direct, const void** w,
+                         int* w_is_float) = 0;
   virtual int prog_size(int prog) const = 0;
   virtual int64_t prog_bytes(int prog) const = 0;
 };
@@ -862,6 +865,12 @@ struct FactorT : FactorBase {
   std::vector<std::unique_ptr<Program<T>>> progs;
   int apply(int prog, const double* r, double* zz, int transpose, cudaStream_t st, bool direct) override {
     return apply_impl<T>(this, *progs[prog], r, zz, transpose, st, direct);
+  }
+  int apply_slot(int prog, const double* r, int transpose, cudaStream_t st, bool direct, const void** wout,
+                 int* w_is_float) override {
+    *wout = w + progs[prog]->off;
+    *w_is_float = std::is_same<T, float>::value ? 1 : 0;
+    return apply_impl<T>(this, *progs[prog], r, nullptr, transpose, st, direct);
   }
   int prog_size(int prog) const override { return progs[prog]->N; }
   int64_t prog_bytes(int prog) const override { return progs[prog]->bytes; }
@@ -2267,8 +2276,10 @@ int apply_impl(FactorT<T>* F, Program<T>& pg, const double* r, double* zout, int
       run_phases<T>(bwd, st);
     }
   }
-  note_launch();
-  k_convert<T, double><<<g, 256, 0, st>>>(w, zout, N);
+  if (zout) {                   // zout == nullptr: the caller reads the factor's vector itself
+    note_launch();
+    k_convert<T, double><<<g, 256, 0, st>>>(w, zout, N);
+  }
   SPAND_CUDA_TRY(cudaGetLastError());
   return SPAND_OK;
 }
@@ -2318,6 +2329,10 @@ int factor_apply(spand_factor_t F, const double* r, double* z, int transpose, cu
   return F->impl->apply(F->prog, r, z, transpose, st, direct);
 }
 int factor_size(spand_factor_t F) { return F->impl->prog_size(F->prog); }
+int factor_apply_slot(spand_factor_t F, const double* r, int transpose, cudaStream_t st, bool direct, const void** w,
+                      int* w_is_float) {
+  return F->impl->apply_slot(F->prog, r, transpose, st, direct, w, w_is_float);
+}
 }  // namespace spand
 
 extern "C" {

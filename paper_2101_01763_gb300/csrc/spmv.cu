@@ -18,9 +18,12 @@ namespace spand {
 // columns w*cs .. w*cs+cs-1 of every block of the row, and warp 0 adds the 8
 // partial sums: eight times as many threads as rows and an eighth of the
 // dependent loads per thread.
+// x may be FP64 or FP32 (the FP32 preconditioner's own output vector, read in
+// place by the matrix-powers step); the products are accumulated in FP64.
+template <typename TX>
 __global__ void __launch_bounds__(256) k_bsr_spmv(int K, int B, const int* __restrict__ row_ptr,
                                                         const int* __restrict__ col, const double* __restrict__ val,
-                                                        const double* __restrict__ x, double* __restrict__ y,
+                                                        const TX* __restrict__ x, double* __restrict__ y,
                                                         double sa, double a1, const double* __restrict__ u1,
                                                         double a2, const double* __restrict__ u2) {
   __shared__ double part[8][33];
@@ -35,13 +38,13 @@ __global__ void __launch_bounds__(256) k_bsr_spmv(int K, int B, const int* __res
     double s1 = 0;
     for (int k = row_ptr[e]; k < row_ptr[e + 1]; ++k) {
       const double* blk = val + (size_t)k * bb + r;
-      const double* xv = x + (size_t)col[k] * B;
+      const TX* xv = x + (size_t)col[k] * B;
       int c = c0;
       for (; c + 2 <= c1; c += 2) {
-        s += __ldg(blk + (size_t)c * B) * __ldg(xv + c);
-        s1 += __ldg(blk + (size_t)(c + 1) * B) * __ldg(xv + c + 1);
+        s += __ldg(blk + (size_t)c * B) * (double)__ldg(xv + c);
+        s1 += __ldg(blk + (size_t)(c + 1) * B) * (double)__ldg(xv + c + 1);
       }
-      if (c < c1) s += __ldg(blk + (size_t)c * B) * __ldg(xv + c);
+      if (c < c1) s += __ldg(blk + (size_t)c * B) * (double)__ldg(xv + c);
     }
     s += s1;
   }
@@ -59,9 +62,10 @@ __global__ void __launch_bounds__(256) k_bsr_spmv(int K, int B, const int* __res
 }
 
 // y = A^T x: row e' of A^T gathers block (e, e') of every neighbour e (symmetric pattern)
+template <typename TX>
 __global__ void __launch_bounds__(256) k_bsr_spmv_t(int K, int B, const int* __restrict__ row_ptr,
                                                     const int* __restrict__ col, const double* __restrict__ val,
-                                                    const double* __restrict__ x, double* __restrict__ y, double sa,
+                                                    const TX* __restrict__ x, double* __restrict__ y, double sa,
                                                     double a1, const double* __restrict__ u1, double a2,
                                                     const double* __restrict__ u2) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -76,8 +80,8 @@ __global__ void __launch_bounds__(256) k_bsr_spmv_t(int K, int B, const int* __r
       if (col[k] == ep) kk = k;
     if (kk < 0) continue;
     const double* blk = val + (size_t)kk * bb + (size_t)c * B;   // column c of block (e, e')
-    const double* xv = x + (size_t)e * B;
-    for (int r = 0; r < B; ++r) s += blk[r] * xv[r];
+    const TX* xv = x + (size_t)e * B;
+    for (int r = 0; r < B; ++r) s += blk[r] * (double)xv[r];
   }
   double v = sa * s;
   if (u1) v += a1 * u1[g];
@@ -85,17 +89,30 @@ __global__ void __launch_bounds__(256) k_bsr_spmv_t(int K, int B, const int* __r
   y[g] = v;
 }
 
-int spmv_fused(const bsr_matrix* A, const double* x, double* y, int transpose, double sa, double a1,
-               const double* u1, double a2, const double* u2, cudaStream_t st) {
+template <typename TX>
+static int spmv_launch(const bsr_matrix* A, const TX* x, double* y, int transpose, double sa, double a1,
+                       const double* u1, double a2, const double* u2, cudaStream_t st) {
   const int64_t n = (int64_t)A->K * A->B;
   const unsigned g = (unsigned)((n + 255) / 256);
   note_launch();
   if (!transpose)
-    k_bsr_spmv<<<(unsigned)((n + 31) / 32), 256, 0, st>>>(A->K, A->B, A->row_ptr, A->col, A->val, x, y, sa,
-                                                               a1, u1, a2, u2);
+    k_bsr_spmv<TX><<<(unsigned)((n + 31) / 32), 256, 0, st>>>(A->K, A->B, A->row_ptr, A->col, A->val, x, y, sa,
+                                                                   a1, u1, a2, u2);
   else
-    k_bsr_spmv_t<<<g, 256, 0, st>>>(A->K, A->B, A->row_ptr, A->col, A->val, x, y, sa, a1, u1, a2, u2);
+    k_bsr_spmv_t<TX><<<g, 256, 0, st>>>(A->K, A->B, A->row_ptr, A->col, A->val, x, y, sa, a1, u1, a2, u2);
   return cudaGetLastError() == cudaSuccess ? SPAND_OK : SPAND_ERR_CUDA;
+}
+
+int spmv_fused(const bsr_matrix* A, const double* x, double* y, int transpose, double sa, double a1,
+               const double* u1, double a2, const double* u2, cudaStream_t st) {
+  return spmv_launch<double>(A, x, y, transpose, sa, a1, u1, a2, u2, st);
+}
+
+int spmv_fused_x(const bsr_matrix* A, const void* x, int x_is_float, double* y, int transpose, double sa, double a1,
+                 const double* u1, double a2, const double* u2, cudaStream_t st) {
+  if (x_is_float)
+    return spmv_launch<float>(A, static_cast<const float*>(x), y, transpose, sa, a1, u1, a2, u2, st);
+  return spmv_launch<double>(A, static_cast<const double*>(x), y, transpose, sa, a1, u1, a2, u2, st);
 }
 
 // ------------------------------------------------------------------ Gram: G = Z^T Y
