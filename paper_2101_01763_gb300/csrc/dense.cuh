@@ -20,6 +20,7 @@
 namespace spand {
 
 constexpr int LU_NB = 32;
+constexpr int LU_NB2 = 128;   // columns per block of the two-level LU
 
 template <typename T>
 struct MatRef {      // square matrix for getrf / inverses
@@ -153,8 +154,10 @@ __device__ inline T warp_sum(T v) {
 // Factor columns k0..k0+jb-1 of every matrix (rows k0..n-1) with partial
 // pivoting, swap whole rows, then U12 = L11^-1 A12.  flags[0] |= 1 on an exact
 // zero pivot, flags[0] |= 2 on a non-finite pivot.
+// Row interchanges reach every column; U12 = L11^-1 A12 is formed for the
+// columns in [k0 + jb, tcol) (the rest wait for the end of their block).
 template <typename T>
-__global__ void __launch_bounds__(256) k_getrf_panel(const MatRef<T>* mats, int nmat, int k0, int* flags) {
+__global__ void __launch_bounds__(256) k_getrf_panel(const MatRef<T>* mats, int nmat, int k0, int tcol, int* flags) {
   __shared__ T sv[32];
   __shared__ int si[32];
   __shared__ T L11[LU_NB][LU_NB + 1];
@@ -204,7 +207,8 @@ __global__ void __launch_bounds__(256) k_getrf_panel(const MatRef<T>* mats, int 
     L11[r][c] = A[(k0 + r) + (size_t)(k0 + c) * ld];
   }
   __syncthreads();
-  for (int c = k0 + jb + threadIdx.x; c < n; c += blockDim.x) {
+  const int cend = min(n, tcol);
+  for (int c = k0 + jb + threadIdx.x; c < cend; c += blockDim.x) {
     T x[LU_NB];
     T* col = A + (size_t)c * ld + k0;
 #pragma unroll
@@ -359,7 +363,8 @@ struct LuColTile {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_getrf_swap_trsm(const MatRef<T>* mats, const LuColTile* tiles, int k0) {
+__global__ void __launch_bounds__(256) k_getrf_swap_trsm(const MatRef<T>* mats, const LuColTile* tiles, int k0,
+                                                         int tcol) {
   __shared__ T L11[LU_NB][LU_NB + 1];
   __shared__ int s_pos[2 * LU_NB], s_src[2 * LU_NB];
   __shared__ int s_cnt;
@@ -394,7 +399,7 @@ __global__ void __launch_bounds__(256) k_getrf_swap_trsm(const MatRef<T>* mats, 
     if (lane < cnt) colp[s_pos[lane]] = v0;
     if (lane + 32 < cnt) colp[s_pos[lane + 32]] = v1;
     __syncwarp();
-    if (col >= k0 + jb) {
+    if (col >= k0 + jb && col < tcol) {
       // U12 column: x = L11^-1 x over rows k0 .. k0+jb-1
       T x = (lane < jb) ? colp[lane] : (T)0;
       for (int q = 0; q < jb - 1; ++q) {
@@ -403,6 +408,36 @@ __global__ void __launch_bounds__(256) k_getrf_swap_trsm(const MatRef<T>* mats, 
       }
       if (lane < jb) colp[lane] = x;
     }
+  }
+}
+
+// The end of a block of panels: rows k0 .. k0+jb-1 of the columns right of
+// the block become U12 = L11^-1 A12 (the row interchanges have already
+// reached them).  tiles[].c0: first column of a 32-column tile.
+template <typename T>
+__global__ void __launch_bounds__(256) k_lu_trsm_cols(const MatRef<T>* mats, const LuColTile* tiles, int k0) {
+  __shared__ T L11[LU_NB][LU_NB + 1];
+  const LuColTile tl = tiles[blockIdx.x];
+  const MatRef<T> M = mats[tl.mat];
+  const int n = M.n;
+  const size_t ld = n;
+  const int jb = min(LU_NB, n - k0);
+  for (int t = threadIdx.x; t < LU_NB * LU_NB; t += blockDim.x) {
+    const int r = t % LU_NB, c = t / LU_NB;
+    L11[r][c] = (r < jb && c < jb) ? M.A[(k0 + r) + (size_t)(k0 + c) * ld] : (T)0;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int cc = wid; cc < 32; cc += 8) {
+    const int col = tl.c0 + cc;
+    if (col >= n) break;
+    T* colp = M.A + (size_t)col * ld + k0;
+    T x = (lane < jb) ? colp[lane] : (T)0;
+    for (int q = 0; q < jb - 1; ++q) {
+      const T xq = __shfl_sync(0xffffffffu, x, q);
+      if (lane > q) x -= L11[lane][q] * xq;
+    }
+    if (lane < jb) colp[lane] = x;
   }
 }
 

@@ -25,6 +25,7 @@
 #include <memory>
 #include <new>
 #include <type_traits>
+#include <string>
 #include <vector>
 
 #include "dense.cuh"
@@ -346,9 +347,45 @@ static int gemm_pick(double avg_chunks, double flops, cudaEvent_t& e0, cudaEvent
   return rule;                       // both measurements still in flight
 }
 
+// SPAND_DEBUG=3: CUDA-event time, logical flops and kernel of every grouped
+// GEMM launch, summed per purpose (tag) and printed when the factorization ends
+struct GemmLog {
+  struct Rec {
+    const char* tag;
+    int kind;                // 0 tcgen05, 1 mma.sync, 2 FP64
+    double flops;
+    size_t tiles;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  static GemmLog& get() {
+    static GemmLog* g = new GemmLog();
+    return *g;
+  }
+  void print_and_clear() {
+    std::map<std::string, std::array<double, 4>> agg;   // ms, flops, launches, tiles
+    for (auto& r : recs) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) cudaGetLastError();
+      auto& a = agg[std::string(r.tag) + (r.kind == 0 ? " tcgen05" : r.kind == 1 ? " mma.sync" : " fp64")];
+      a[0] += ms;
+      a[1] += r.flops;
+      a[2] += 1;
+      a[3] += (double)r.tiles;
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    recs.clear();
+    for (auto& kv : agg)
+      std::fprintf(stderr, "spand: GEMM %-22s %8.2f ms %10.3g flops %6.0f launches %10.0f tiles %7.1f TFLOP/s\n",
+                   kv.first.c_str(), kv.second[0], kv.second[1], kv.second[2], kv.second[3],
+                   kv.second[0] > 0 ? kv.second[1] / (kv.second[0] * 1e9) : 0.0);
+  }
+};
+
 template <typename T>
 static void launch_gemm(DevMem& tmp, const std::vector<GemmTask<T>>& tasks, const std::vector<GemmTerm<T>>& terms,
-                        cudaStream_t st) {
+                        cudaStream_t st, const char* tag = "") {
   bool umma = false;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (std::is_same<T, float>::value) {
@@ -379,6 +416,20 @@ static void launch_gemm(DevMem& tmp, const std::vector<GemmTask<T>>& tasks, cons
   upload3(tmp, tasks, terms, tiles, dt, dm, dl);
   if (tmp.err) return;
   note_launch();
+  GemmLog::Rec rec{tag, std::is_same<T, float>::value ? (umma ? 0 : 1) : 2, 0.0, tiles.size(), nullptr, nullptr};
+  const bool logit = debug_level() >= 3 && cudaEventCreate(&rec.a) == cudaSuccess &&
+                     cudaEventCreate(&rec.b) == cudaSuccess && cudaEventRecord(rec.a, st) == cudaSuccess;
+  if (logit)
+    for (const auto& tk : tasks)
+      for (int t = tk.t0; t < tk.t1; ++t) rec.flops += 2.0 * tk.m * (double)tk.n * terms[t].k;
+  struct LogAtEnd {
+    bool on;
+    GemmLog::Rec& r;
+    cudaStream_t s;
+    ~LogAtEnd() {
+      if (on && cudaEventRecord(r.b, s) == cudaSuccess) GemmLog::get().recs.push_back(r);
+    }
+  } log_at_end{logit, rec, st};
   if constexpr (std::is_same<T, float>::value) {
     if (e0) cudaEventRecord(e0, st);
     if (umma && v1) {
@@ -648,7 +699,16 @@ static void batched_getrf(DevMem& tmp, std::vector<MatRef<T>>& mats, int* d_flag
     set_dyn_smem((const void*)k_getrf_panel_smem<T>, LU_SMEM_BYTES);
     set_dyn_smem((const void*)k_ipiv_to_perm<T>, 200 * 1024);
   });
+  // Two-level blocking (the arrangement of LAPACK's blocked getrf): panels of
+  // LU_NB columns are grouped in blocks of LU_NB2.  Inside a block a panel's
+  // row interchanges reach every column, but its TRSM and its rank-LU_NB
+  // update touch only the block's own columns; the columns right of the block
+  // stay un-updated (so interchanging their rows is consistent).  When the
+  // block is done, their rows K0..Ke-1 become U12 (staged TRSM, one panel's
+  // rows at a time) and the rest takes one rank-(Ke-K0) update.
   for (int k0 = 0; k0 < nmax; k0 += LU_NB) {
+    const int K0 = k0 / LU_NB2 * LU_NB2;
+    const int tcol = K0 + LU_NB2;            // TRSM / updates inside the block only
     if (ds && k0 < nsmall_max) {
       const size_t sm = (size_t)(nsmall_max - k0) * std::min(LU_NB, nsmall_max - k0) * sizeof(T);
       note_launch();
@@ -665,25 +725,70 @@ static void batched_getrf(DevMem& tmp, std::vector<MatRef<T>>& mats, int* d_flag
         auto* dtl = tmp.upload(tl);
         if (tmp.err) return;
         note_launch();
-        k_getrf_swap_trsm<T><<<(unsigned)tl.size(), 256, 0, st>>>(ds, dtl, k0);
+        k_getrf_swap_trsm<T><<<(unsigned)tl.size(), 256, 0, st>>>(ds, dtl, k0, tcol);
       }
     }
     if (dlg) {
       note_launch();
-      k_getrf_panel<T><<<(unsigned)large.size(), 256, 0, st>>>(dlg, (int)large.size(), k0, d_flags);
+      k_getrf_panel<T><<<(unsigned)large.size(), 256, 0, st>>>(dlg, (int)large.size(), k0, tcol, d_flags);
     }
+    // rank-LU_NB update of the block's columns [r, Ke), every row below the panel
     std::vector<GemmTask<T>> tasks;
     std::vector<GemmTerm<T>> terms;
+    bool block_end = false;
     for (auto& m : mats) {
       const int n = m.n;
       if (k0 + LU_NB >= n) continue;
-      const int jb = LU_NB, r = k0 + jb, rem = n - r;
-      GemmTerm<T> tm{m.A + r + (size_t)k0 * n, m.A + k0 + (size_t)r * n, n, n, jb, 0, 0, 0};
-      GemmTask<T> tk{m.A + r + (size_t)r * n, n, rem, rem, (T)-1, (T)1, (int)terms.size(), (int)terms.size() + 1};
-      terms.push_back(tm);
-      tasks.push_back(tk);
+      const int jb = LU_NB, r = k0 + jb, Ke = std::min(tcol, n);
+      if (Ke > r) {
+        terms.push_back({m.A + r + (size_t)k0 * n, m.A + k0 + (size_t)r * n, n, n, jb, 0, 0, 0});
+        tasks.push_back({m.A + r + (size_t)r * n, n, n - r, Ke - r, (T)-1, (T)1, (int)terms.size() - 1,
+                         (int)terms.size()});
+      } else if (n > Ke) {
+        block_end = true;
+      }
     }
-    launch_gemm(tmp, tasks, terms, st);
+    launch_gemm(tmp, tasks, terms, st, "lu-trailing");
+    if (!block_end) continue;
+    // the block [K0, Ke) is done: rows K0..Ke-1 of the columns right of it,
+    // one panel's rows at a time (TRSM, then the rank-LU_NB update of the
+    // block rows below), then everything right of and below the block
+    for (int p0 = K0; p0 < tcol; p0 += LU_NB) {
+      std::vector<LuColTile> tl;
+      std::vector<MatRef<T>> sub;
+      std::vector<GemmTask<T>> rt;
+      std::vector<GemmTerm<T>> rm;
+      for (auto& m : mats) {
+        const int n = m.n;
+        if (n <= tcol || p0 >= n) continue;  // only matrices whose block ended here with columns right of it
+        const int b = (int)sub.size();
+        sub.push_back(m);
+        for (int c0 = tcol; c0 < n; c0 += 32) tl.push_back({b, c0});
+        const int r = p0 + LU_NB;
+        if (r < tcol) {
+          rm.push_back({m.A + r + (size_t)p0 * n, m.A + p0 + (size_t)tcol * n, n, n, LU_NB, 0, 0, 0});
+          rt.push_back({m.A + r + (size_t)tcol * n, n, tcol - r, n - tcol, (T)-1, (T)1, (int)rm.size() - 1,
+                        (int)rm.size()});
+        }
+      }
+      if (tl.empty()) break;
+      auto* dsub = tmp.upload(sub);
+      auto* dtl = tmp.upload(tl);
+      if (tmp.err) return;
+      note_launch();
+      k_lu_trsm_cols<T><<<(unsigned)tl.size(), 256, 0, st>>>(dsub, dtl, p0);
+      launch_gemm(tmp, rt, rm, st, "lu-block-rows");
+    }
+    std::vector<GemmTask<T>> bt;
+    std::vector<GemmTerm<T>> bm;
+    for (auto& m : mats) {
+      const int n = m.n;
+      if (n <= tcol) continue;
+      bm.push_back({m.A + tcol + (size_t)K0 * n, m.A + K0 + (size_t)tcol * n, n, n, tcol - K0, 0, 0, 0});
+      bt.push_back({m.A + tcol + (size_t)tcol * n, n, n - tcol, n - tcol, (T)-1, (T)1, (int)bm.size() - 1,
+                    (int)bm.size()});
+    }
+    launch_gemm(tmp, bt, bm, st, "lu-block");
   }
   note_launch();
   k_ipiv_to_perm<T><<<(unsigned)mats.size(), 128, (size_t)nmax * sizeof(int), st>>>(dm, (int)mats.size());
@@ -764,8 +869,8 @@ static void batched_inverses(DevMem& tmp, const std::vector<MatRef<T>>& mats, co
         t2.push_back({Uinv[b] + a0 + (size_t)c0 * n, n, na, nc, (T)-1, (T)0, (int)m2.size() - 1, (int)m2.size()});
       }
     }
-    launch_gemm(tmp, t1, m1, st);
-    launch_gemm(tmp, t2, m2, st);
+    launch_gemm(tmp, t1, m1, st, "tri-inverse");
+    launch_gemm(tmp, t2, m2, st, "tri-inverse");
   }
   // scalings of the interface form: SL = diag(1/d) L^-1, SU = U^-1 diag(d)
   std::vector<InvTask<T>> lt, ut;
@@ -1197,7 +1302,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       double gflops = 0;
       for (size_t q = 0; q < tasks.size(); ++q) gflops += 1.0 * tasks[q].m * (double)tasks[q].n * terms[q].k;
       ev_begin(ev_gm[l]);
-      launch_gemm(tmp, tasks, terms, st);
+      launch_gemm(tmp, tasks, terms, st, "elim-YX");
       // Schur updates grouped by target block
       std::map<std::pair<int, int>, std::vector<int>> contrib;
       for (int s : I)
@@ -1216,7 +1321,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
         tasks.push_back({blk(a, b), n[a], n[a], n[b], (T)-1, (T)1, t0, (int)terms.size()});
         for (int q = t0; q < (int)terms.size(); ++q) gflops += 2.0 * n[a] * (double)n[b] * terms[q].k;
       }
-      launch_gemm(tmp, tasks, terms, st);
+      launch_gemm(tmp, tasks, terms, st, "elim-schur");
       ev_end(ev_gm[l]);
       S.elim_gemm_flops += gflops;
       S.elim_gemm_launches += 2;
@@ -1294,8 +1399,8 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       }
       if (tmp.err) return SPAND_ERR_NOMEM;
       launch_row_perm(tmp, ps, pd, pp, pr_, pc_, st);
-      launch_gemm(tmp, t1, m1, st);
-      launch_gemm(tmp, t2, m2, st);
+      launch_gemm(tmp, t1, m1, st, "scale");
+      launch_gemm(tmp, t2, m2, st, "scale");
     }
     mark(2);
     // ================= 3. all Q first (Eq. 12): RRQR of [A_sn A_ns^T]
@@ -1828,7 +1933,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
         qtk.push_back({qt[q].Q, nn, nn, r, (T)-1, (T)1, (int)qm.size() - 1, (int)qm.size()});
       }
       if (tmp.err) return SPAND_ERR_NOMEM;
-      launch_gemm(tmp, gt, gm, st);
+      launch_gemm(tmp, gt, gm, st, "wy");
       if (!wy.empty()) {
         auto* dw = tmp.upload(wy);
         note_launch();
@@ -1839,8 +1944,8 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
         note_launch();
         k_eye<T><<<std::min<unsigned>((unsigned)eye_q.size(), 1024), 128, 0, st>>>(de, (int)eye_q.size());
       }
-      launch_gemm(tmp, mt, mm, st);
-      launch_gemm(tmp, qtk, qm, st);
+      launch_gemm(tmp, mt, mm, st, "wy");
+      launch_gemm(tmp, qtk, qm, st, "wy");
     }
     // records for the apply
     for (size_t q = 0; q < Fc.size(); ++q) {
@@ -1906,8 +2011,8 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       flops += 2.0 * n[a] * (double)n[b] * (r[a] + r[b]);
     }
     if (tmp.err) return SPAND_ERR_NOMEM;
-    launch_gemm(tmp, t1, m1, st);
-    launch_gemm(tmp, t2, m2, st);
+    launch_gemm(tmp, t1, m1, st, "compress");
+    launch_gemm(tmp, t2, m2, st, "compress");
     if (!eyes.empty()) {
       auto* de = tmp.upload(eyes);
       note_launch();
@@ -1939,6 +2044,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
     }
   }
   S.factor_flops = flops;
+  if (debug_level() >= 3) GemmLog::get().print_and_clear();
 
   mark(6);
   // ================= apply program

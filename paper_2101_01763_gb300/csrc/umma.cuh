@@ -23,7 +23,9 @@
 
 namespace spand {
 
-constexpr int UM_BM = 128, UM_BN = 64, UM_BK = 32;
+constexpr int UM_BM = 128, UM_BN = 64, UM_BK = 16;
+constexpr int UM_BH = UM_BK / 2;          // k values of a B column one thread stages
+constexpr int UM_SBO = 8 * UM_BK * 4;     // bytes between 8-row groups of a K-major operand
 constexpr int UM_TMEM_COLS = 64;
 // bytes of one operand stage: A hi, A lo (128 x 32 x 4), B hi, B lo (64 x 32 x 4)
 constexpr int UM_A_BYTES = UM_BM * UM_BK * 4, UM_B_BYTES = UM_BN * UM_BK * 4;
@@ -54,6 +56,10 @@ __host__ __device__ constexpr uint32_t umma_idesc_tf32() {
 __device__ inline uint32_t umma_off(int r, int k) {
   return (uint32_t)((r >> 3) * 1024 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4);
 }
+// the same for UM_BK-wide k-chunks (8-row groups UM_SBO bytes apart)
+__device__ inline uint32_t umma_off_bk(int r, int k) {
+  return (uint32_t)((r >> 3) * UM_SBO + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4);
+}
 
 __device__ inline bool mbar_wait(uint32_t bar, uint32_t parity) {
   for (long it = 0; it < (1l << 24); ++it) {
@@ -70,7 +76,7 @@ __device__ inline bool mbar_wait(uint32_t bar, uint32_t parity) {
 
 __device__ int g_umma_fail;   // set when an MMA completion wait ran out of time
 
-__global__ void __launch_bounds__(128, 2) k_gemm_umma(const GemmTask<float>* tasks, const GemmTerm<float>* terms,
+__global__ void __launch_bounds__(128, 4) k_gemm_umma(const GemmTask<float>* tasks, const GemmTerm<float>* terms,
                                                       const TileItem* tiles) {
   extern __shared__ unsigned char um_raw[];
   __shared__ uint64_t mbar[2];
@@ -104,12 +110,12 @@ __global__ void __launch_bounds__(128, 2) k_gemm_umma(const GemmTask<float>* tas
   while (cur_t < tk.t1 && term_klim(terms[cur_t], i0, j0, UM_BM, UM_BN) <= 0) ++cur_t;
   int item = 0;
   bool failed = false;
-  // operand values of one k-chunk held in registers: this thread's A row (32 k)
-  // and half of one B column (16 k).  The loads of chunk i+1 are issued right
+  // operand values of one k-chunk held in registers: this thread's A row (UM_BK k)
+  // and half of one B column (UM_BH k).  The loads of chunk i+1 are issued right
   // after the MMAs of chunk i, so their latency overlaps the tensor-core work.
   const int r = tid, gi = i0 + r;
   const int c = tid & 63, half = tid >> 6, gj = j0 + c;
-  float x[UM_BK], y[16];
+  float x[UM_BK], y[UM_BH];
   auto load_chunk = [&](int t_, int l_) {
     const GemmTerm<float> tm = terms[t_];
     const bool a_vec = tm.ta && ((tm.lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(tm.A) & 15) == 0) &&
@@ -132,13 +138,13 @@ __global__ void __launch_bounds__(128, 2) k_gemm_umma(const GemmTask<float>* tas
                                         : 0.f;
       }
     }
-    const int kb = l_ + half * 16;
+    const int kb = l_ + half * UM_BH;
     const bool b_vec = !tm.tb && ((tm.ldb & 3) == 0) && ((reinterpret_cast<uintptr_t>(tm.B) & 15) == 0) &&
-                       kb + 16 <= tm.k;
+                       kb + UM_BH <= tm.k;
     if (b_vec && gj < tk.n) {
       const float4* src = reinterpret_cast<const float4*>(tm.B + kb + (size_t)gj * tm.ldb);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < UM_BH / 4; ++q) {
         const float4 f = src[q];
         y[4 * q] = f.x;
         y[4 * q + 1] = f.y;
@@ -147,7 +153,7 @@ __global__ void __launch_bounds__(128, 2) k_gemm_umma(const GemmTask<float>* tas
       }
     } else {
 #pragma unroll
-      for (int e = 0; e < 16; ++e) {
+      for (int e = 0; e < UM_BH; ++e) {
         const int gl = kb + e;
         y[e] = (gj < tk.n && gl < tm.k) ? (tm.tb ? tm.B[gj + (size_t)gl * tm.ldb] : tm.B[gl + (size_t)gj * tm.ldb])
                                         : 0.f;
@@ -180,12 +186,12 @@ __global__ void __launch_bounds__(128, 2) k_gemm_umma(const GemmTask<float>* tas
         lo.y = to_tf32(x[kq + 1] - __uint_as_float(hi.y));
         lo.z = to_tf32(x[kq + 2] - __uint_as_float(hi.z));
         lo.w = to_tf32(x[kq + 3] - __uint_as_float(hi.w));
-        const uint32_t off = umma_off(r, kq);
+        const uint32_t off = umma_off_bk(r, kq);
         *reinterpret_cast<uint4*>(st + off) = hi;
         *reinterpret_cast<uint4*>(st + UM_A_BYTES + off) = lo;
       }
 #pragma unroll
-      for (int kq = 0; kq < 16; kq += 4) {
+      for (int kq = 0; kq < UM_BH; kq += 4) {
         uint4 hi, lo;
         hi.x = to_tf32(y[kq]);
         hi.y = to_tf32(y[kq + 1]);
@@ -195,7 +201,7 @@ __global__ void __launch_bounds__(128, 2) k_gemm_umma(const GemmTask<float>* tas
         lo.y = to_tf32(y[kq + 1] - __uint_as_float(hi.y));
         lo.z = to_tf32(y[kq + 2] - __uint_as_float(hi.z));
         lo.w = to_tf32(y[kq + 3] - __uint_as_float(hi.w));
-        const uint32_t off = umma_off(c, half * 16 + kq);
+        const uint32_t off = umma_off_bk(c, half * UM_BH + kq);
         *reinterpret_cast<uint4*>(st + 2 * UM_A_BYTES + off) = hi;
         *reinterpret_cast<uint4*>(st + 2 * UM_A_BYTES + UM_B_BYTES + off) = lo;
       }
@@ -211,8 +217,8 @@ __global__ void __launch_bounds__(128, 2) k_gemm_umma(const GemmTask<float>* tas
 #pragma unroll
       for (int ks = 0; ks < UM_BK / 8; ++ks) {
         const uint32_t ko = ks * 256;            // two core matrices along K per 8-wide step
-        const uint64_t dah = umma_desc(a_hi + ko, 128, 1024), dal = umma_desc(a_lo + ko, 128, 1024);
-        const uint64_t dbh = umma_desc(b_hi + ko, 128, 1024), dbl = umma_desc(b_lo + ko, 128, 1024);
+        const uint64_t dah = umma_desc(a_hi + ko, 128, UM_SBO), dal = umma_desc(a_lo + ko, 128, UM_SBO);
+        const uint64_t dbh = umma_desc(b_hi + ko, 128, UM_SBO), dbl = umma_desc(b_lo + ko, 128, UM_SBO);
         const uint32_t acc0 = (item > 0 || ks > 0) ? 1u : 0u;
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
