@@ -349,7 +349,15 @@ int sstep_gmres_solve_batched(int nsys, const bsr_matrix* A, const spand_factor_
  *    problems are rejected with SPAND_ERR_SCRATCH before any work is queued.
  *  - The first call on each device looks up the array's device address (with
  *    that device current) and caches it; make that first call before any
- *    stream capture.
+ *    stream capture.  The array and the library's kernels are loaded into
+ *    device memory when first used (the CUDA runtime loads modules lazily), so
+ *    a caller that then hands all remaining device memory to its own pool
+ *    should make one call (or one regular solve) on each device first.
+ *  - The preconditioner's launches go on the stream one by one: its CUDA graph
+ *    (built on first use by spand_apply and sstep_gmres_solve, and building
+ *    it allocates) is neither built nor used here, so a factor that was never
+ *    applied takes no memory either.  Like sstep_gmres_solve, the call
+ *    synchronizes its stream to read residual estimates during the solve.
  *  - Every call on a device shares the one array and it keeps the previous
  *    call's contents (the solver clears what it needs zeroed).  Calls whose
  *    work overlaps on the GPU (other streams, other host threads) race on the

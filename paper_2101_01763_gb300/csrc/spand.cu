@@ -464,20 +464,28 @@ static void launch_copy(DevMem& tmp, const std::vector<CopyTask<T>>& tasks, cuda
   k_copy_tiles<T><<<(unsigned)tiles.size(), 256, 0, st>>>(dt, dl);
 }
 
-// row-permuted copy: dst[r, c] = src[perm[r], c]; one CTA per task
+// row-permuted copy: dst[r, c] = src[perm[r], c]; one CTA per 64 x 32 tile
+// (rows x columns) of a task, a warp per column pair, lanes over rows
+struct RowPermTask {
+  const void* src;
+  void* dst;
+  const int* perm;
+  int rows, cols;
+};
+struct RowPermTile {
+  int task, r0, c0;
+};
+
 template <typename T>
-__global__ void k_row_perm(const T* const* src, T* const* dst, const int* const* perm, const int* rows,
-                           const int* cols) {
-  const int t = blockIdx.x;
-  const int n = rows[t], m = cols[t];
-  const size_t tot = (size_t)n * m;
-  const T* s = src[t];
-  T* d = dst[t];
-  const int* p = perm[t];
-  for (size_t idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-    const int r = (int)(idx % n);
-    const size_t c = idx / n;
-    d[r + c * n] = s[p[r] + c * n];
+__global__ void __launch_bounds__(256) k_row_perm(const RowPermTask* tasks, const RowPermTile* tiles) {
+  const RowPermTile tl = tiles[blockIdx.x];
+  const RowPermTask tk = tasks[tl.task];
+  const T* s = static_cast<const T*>(tk.src);
+  T* d = static_cast<T*>(tk.dst);
+  const int n = tk.rows;
+  for (int idx = threadIdx.x; idx < 64 * 32; idx += blockDim.x) {
+    const int r = tl.r0 + (idx & 63), c = tl.c0 + (idx >> 6);
+    if (r < n && c < tk.cols) d[r + (size_t)c * n] = s[tk.perm[r] + (size_t)c * n];
   }
 }
 
@@ -486,14 +494,20 @@ static void launch_row_perm(DevMem& tmp, const std::vector<const T*>& src, const
                             const std::vector<const int*>& perm, const std::vector<int>& rows,
                             const std::vector<int>& cols, cudaStream_t st) {
   if (src.empty()) return;
-  auto* a = tmp.upload(src);
-  auto* b = tmp.upload(dst);
-  auto* c = tmp.upload(perm);
-  auto* d = tmp.upload(rows);
-  auto* e = tmp.upload(cols);
+  std::vector<RowPermTask> tasks(src.size());
+  std::vector<RowPermTile> tiles;
+  for (size_t t = 0; t < src.size(); ++t) {
+    tasks[t] = {src[t], dst[t], perm[t], rows[t], cols[t]};
+    for (int r0 = 0; r0 < rows[t]; r0 += 64)
+      for (int c0 = 0; c0 < cols[t]; c0 += 32) tiles.push_back({(int)t, r0, c0});
+  }
+  if (tiles.empty()) return;
+  RowPermTask* dt;
+  RowPermTile* dl;
+  upload2(tmp, tasks, tiles, dt, dl);
   if (tmp.err) return;
   note_launch();
-  k_row_perm<T><<<(unsigned)src.size(), 256, 0, st>>>(a, b, c, d, e);
+  k_row_perm<T><<<(unsigned)tiles.size(), 256, 0, st>>>(dt, dl);
 }
 
 // ------------------------------------------------------------------ streaming RRQR launch
@@ -676,23 +690,10 @@ static void batched_getrf(DevMem& tmp, std::vector<MatRef<T>>& mats, int* d_flag
   for (auto& m : mats) nmax = std::max(nmax, m.n);
   auto* dm = tmp.upload(mats);
   if (tmp.err) return;
-  // matrices whose panels fit the shared-memory budget take the staged kernel
-  std::vector<MatRef<T>> small, large;
-  int nsmall_max = 0;
-  for (auto& m : mats) {
-    if ((size_t)m.n * LU_NB * sizeof(T) <= (size_t)LU_SMEM_BYTES) {
-      small.push_back(m);
-      nsmall_max = std::max(nsmall_max, m.n);
-    } else {
-      large.push_back(m);
-    }
-  }
-  if (!small.empty()) {
-    int* aff = tmp.alloc<int>(small.size() * (1 + 4 * LU_NB));
-    for (auto& m : small) m.aff = aff;
-  }
-  auto* ds = small.empty() ? nullptr : tmp.upload(small);
-  auto* dlg = large.empty() ? nullptr : tmp.upload(large);
+  // a panel whose rows fit the shared-memory budget takes the staged kernel,
+  // decided panel by panel (a tall matrix moves to it once its panels shrink);
+  // the staged kernel's interchange records need one slot per matrix
+  int* aff = tmp.alloc<int>(mats.size() * (1 + 4 * LU_NB));
   if (tmp.err) return;
   static std::atomic<uint64_t> attr{0};
   once_per_device(attr, [] {
@@ -709,7 +710,22 @@ static void batched_getrf(DevMem& tmp, std::vector<MatRef<T>>& mats, int* d_flag
   for (int k0 = 0; k0 < nmax; k0 += LU_NB) {
     const int K0 = k0 / LU_NB2 * LU_NB2;
     const int tcol = K0 + LU_NB2;            // TRSM / updates inside the block only
-    if (ds && k0 < nsmall_max) {
+    std::vector<MatRef<T>> small, large;
+    int nsmall_max = 0;
+    for (auto m : mats) {
+      if (k0 >= m.n) continue;
+      if ((size_t)(m.n - k0) * LU_NB * sizeof(T) <= (size_t)LU_SMEM_BYTES) {
+        m.aff = aff;
+        small.push_back(m);
+        nsmall_max = std::max(nsmall_max, m.n);
+      } else {
+        large.push_back(m);
+      }
+    }
+    auto* ds = small.empty() ? nullptr : tmp.upload(small);
+    auto* dlg = large.empty() ? nullptr : tmp.upload(large);
+    if (tmp.err) return;
+    if (ds) {
       const size_t sm = (size_t)(nsmall_max - k0) * std::min(LU_NB, nsmall_max - k0) * sizeof(T);
       note_launch();
       k_getrf_panel_smem<T><<<(unsigned)small.size(), 512, sm, st>>>(ds, (int)small.size(), k0, d_flags);
