@@ -29,6 +29,8 @@
 // wrote it before the barrier and never touches it again) and builds the same
 // reflector; the owner writes it to V.
 #pragma once
+#include <type_traits>
+
 #include "dense.cuh"
 
 namespace spand {
@@ -226,18 +228,32 @@ __device__ inline T qrs_norm2(const T* __restrict__ col, int kb, int n, int lane
   return warp_sum(s);
 }
 
+// FP32 groups exchange their pivot proposals in one word per CTA and step:
+// the proposal's residual norm^2 (float bits, high half) and column index
+// (bits 8..31) with the step's tag (k mod 256, bits 0..7).  A CTA makes its
+// column updates visible, then stores its word; the others poll every word of
+// the group until all carry this step's tag, which is the step's barrier and
+// the proposals' gather in one L2 round trip.  Words are double-buffered by
+// step parity (a CTA is at most one step ahead of the slowest).
+__device__ inline unsigned long long qrs_pack(float v, int i, int k) {
+  return ((unsigned long long)__float_as_uint(v) << 32) | ((unsigned long long)(unsigned)i << 8) |
+         (unsigned long long)(k & 255);
+}
+
 // The factorization of one interface by the CTA of rank q in a group of G
 // (G = 1: a CTA alone, no group barrier).  Gx is the group size the barrier
 // waits for (G, or G + 1 when a test makes the wait run out).
 template <typename T, int NV>
 __device__ bool qrs_task(const QrStreamTask<T>& tk, int q, int G, int Gx, T* prop_v, int* prop_i, GroupSync* gs,
-                         int* err, T eps, long poll_limit, unsigned char* smem) {
+                         unsigned long long* words, int* err, T eps, long poll_limit, unsigned char* smem) {
   using VT = Vec16<T>;
   constexpr int VW = VT::W;
   __shared__ T red_v[QRS_WARPS];
   __shared__ int red_i[QRS_WARPS];
   __shared__ T s_scal[2];
   __shared__ int s_win;
+  __shared__ int s_ok;
+  constexpr bool kWords = std::is_same<T, float>::value;
   GroupX<T> xc{q, Gx, prop_v, prop_i, gs, err, nullptr, 0};
   xc.poll_limit = poll_limit;
   const int n = tk.n, c = tk.c, ldw = tk.ldw;
@@ -284,11 +300,51 @@ __device__ bool qrs_task(const QrStreamTask<T>& tk, int q, int G, int Gx, T* pro
       if (Gx == 1) {
         s_scal[1] = b2;
         s_win = i2;
+      } else if (kWords) {
+        __threadfence();                    // this CTA's column updates before its word
+        volatile unsigned long long* wq = words + (size_t)(k & 1) * QR_GMAX + q;
+        *wq = qrs_pack((float)b2, i2, k);
       } else {
         xc.publish(b2, i2);
       }
     }
-    if (Gx > 1) {
+    if (Gx > 1 && kWords) {
+      __syncthreads();
+      if (tid < 32) {
+        T gb = -1;
+        int gi = c;
+        bool wok = true;
+        for (int r = lane; r < Gx && wok; r += 32) {
+          volatile unsigned long long* wr = words + (size_t)(k & 1) * QR_GMAX + r;
+          unsigned long long w = 0;
+          long it = 0;
+          while (true) {
+            w = *wr;
+            if ((int)(w & 255ull) == (k & 255)) break;
+            if (++it > poll_limit) {
+              wok = false;
+              break;
+            }
+            if (it > 2048) __nanosleep(64);
+          }
+          if (wok) argmax_pair(gb, gi, (T)__uint_as_float((unsigned)(w >> 32)), (int)((w >> 8) & 0xFFFFFFull));
+        }
+        wok = __all_sync(0xffffffffu, wok);
+        __threadfence();                    // the others' column updates are visible from here on
+        warp_argmax(gb, gi);
+        if (lane == 0) {
+          s_scal[1] = gb;
+          s_win = gi;
+          s_ok = wok ? 1 : 0;
+          if (!wok) atomicOr(err, 16);
+        }
+      }
+      __syncthreads();
+      if (!s_ok) {
+        ok = false;
+        break;
+      }
+    } else if (Gx > 1) {
       if (!(ok = xc.sync())) break;
       // ---- group-wide winner
       if (tid < 32) {
@@ -401,8 +457,8 @@ __device__ bool qrs_task(const QrStreamTask<T>& tk, int q, int G, int Gx, T* pro
 template <typename T, int NV>
 __global__ void __launch_bounds__(QRS_THREADS, 1)
     k_qrcp_stream(const QrStreamTask<T>* tasks, const QrGroupDesc* desc, int n_group_ctas, const int* solo,
-                  int n_solo, int* queue, T* prop_v, int* prop_i, GroupSync* gs, int* err, T eps, int poll_log2,
-                  int fault_task) {
+                  int n_solo, int* queue, T* prop_v, int* prop_i, GroupSync* gs, unsigned long long* words,
+                  int* err, T eps, int poll_log2, int fault_task) {
   extern __shared__ __align__(16) unsigned char qrs_smem[];
   __shared__ int s_next;
   const long poll_limit = 1l << poll_log2;
@@ -411,7 +467,8 @@ __global__ void __launch_bounds__(QRS_THREADS, 1)
     const QrGroupDesc d = desc[blockIdx.x];
     const int Gx = d.G + (d.task == fault_task ? 1 : 0);
     ok = qrs_task<T, NV>(tasks[d.task], d.q, d.G, Gx, prop_v + (size_t)d.task * 2 * QR_GMAX,
-                         prop_i + (size_t)d.task * 2 * QR_GMAX, gs + d.task, err, eps, poll_limit, qrs_smem);
+                         prop_i + (size_t)d.task * 2 * QR_GMAX, gs + d.task, words + (size_t)d.task * 2 * QR_GMAX,
+                         err, eps, poll_limit, qrs_smem);
   }
   while (ok) {
     if (threadIdx.x == 0) s_next = atomicAdd(queue, 1);
@@ -422,7 +479,8 @@ __global__ void __launch_bounds__(QRS_THREADS, 1)
     const int task = solo[t];
     const int Gx = 1 + (task == fault_task ? 1 : 0);
     ok = qrs_task<T, NV>(tasks[task], 0, 1, Gx, prop_v + (size_t)task * 2 * QR_GMAX,
-                         prop_i + (size_t)task * 2 * QR_GMAX, gs + task, err, eps, poll_limit, qrs_smem);
+                         prop_i + (size_t)task * 2 * QR_GMAX, gs + task, words + (size_t)task * 2 * QR_GMAX, err,
+                         eps, poll_limit, qrs_smem);
   }
 }
 

@@ -595,9 +595,12 @@ static int launch_stream_once(DevMem& tmp, const QrStreamTask<T>* dt, size_t nt,
   T* pv = tmp.alloc<T>(nt * 2 * QR_GMAX);
   int* pi = tmp.alloc<int>(nt * 2 * QR_GMAX);
   GroupSync* gs = tmp.alloc<GroupSync>(nt);
+  unsigned long long* words = tmp.alloc<unsigned long long>(nt * 2 * QR_GMAX);
   if (tmp.err) return SPAND_ERR_NOMEM;
   SPAND_CUDA_TRY(cudaMemsetAsync(gs, 0, sizeof(GroupSync) * nt, st));
   SPAND_CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(int), st));
+  // every word starts with tag 255, which no word of steps 0 and 1 carries
+  SPAND_CUDA_TRY(cudaMemsetAsync(words, 0xFF, sizeof(unsigned long long) * nt * 2 * QR_GMAX, st));
   int poll_log2 = 22, fault_task = -1;
   if (take_barrier_fault()) {
     fault_task = desc.empty() ? solo[0] : desc[0].task;   // a partner that never arrives
@@ -617,7 +620,7 @@ static int launch_stream_once(DevMem& tmp, const QrStreamTask<T>* dt, size_t nt,
   cfg.numAttrs = 1;
   note_launch();
   SPAND_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, dt, (const QrGroupDesc*)dd, used, (const int*)ds, (int)solo.size(),
-                                    queue, pv, pi, gs, d_flags, eps, poll_log2, fault_task));
+                                    queue, pv, pi, gs, words, d_flags, eps, poll_log2, fault_task));
   return SPAND_OK;
 }
 
@@ -2018,11 +2021,13 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
         eyes.push_back({dst, n2[pa], r[a]});
         continue;
       }
-      // both are sparsified (they have neighbours)
-      T* Tm = tmp.alloc<T>((size_t)r[a] * n[b]);
-      m1.push_back({Qc[a], oblk(a, b), n[a], n[a], n[a], 1, 0, 0});
-      t1.push_back({Tm, r[a], r[a], n[b], (T)1, (T)0, (int)m1.size() - 1, (int)m1.size()});
-      m2.push_back({Tm, Qc[b], r[a], n[b], n[b], 0, 0, 0});
+      // both are sparsified (they have neighbours).  First (Q_ac^T A_ab)^T =
+      // A_ab^T Q_ac (n_b x r_a: the long side along the tiles' 128 rows, both
+      // operands read along k), then Q_ac^T A_ab Q_bc from it
+      T* Tm = tmp.alloc<T>((size_t)n[b] * r[a]);
+      m1.push_back({oblk(a, b), Qc[a], n[a], n[a], n[a], 1, 0, 0});
+      t1.push_back({Tm, n[b], n[b], r[a], (T)1, (T)0, (int)m1.size() - 1, (int)m1.size()});
+      m2.push_back({Tm, Qc[b], n[b], n[b], n[b], 1, 0, 0});
       t2.push_back({dst, n2[pa], r[a], r[b], (T)1, (T)0, (int)m2.size() - 1, (int)m2.size()});
       flops += 2.0 * n[a] * (double)n[b] * (r[a] + r[b]);
     }
