@@ -60,7 +60,7 @@ struct TileItem {
 };
 
 template <typename T>
-struct CopyTask {    // dst[r + c*ldd] = scale * (trans ? src[c + r*lds] : src[r + c*lds])
+struct CopyTask {    // dst[r + c*ldd] = trans ? src[c + r*lds] : src[r + c*lds]
   const T* src;
   T* dst;
   int lds, ldd, rows, cols, trans;
@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(256) k_getrf_panel(const MatRef<T>* mats, int 
   __shared__ T sv[32];
   __shared__ int si[32];
   __shared__ T L11[LU_NB][LU_NB + 1];
+  __shared__ T urow[LU_NB];                 // pivot row segment of the panel
   const int b = blockIdx.x;
   if (b >= nmat) return;
   const MatRef<T> M = mats[b];
@@ -188,15 +189,24 @@ __global__ void __launch_bounds__(256) k_getrf_panel(const MatRef<T>* mats, int 
       }
     __syncthreads();
     const T piv = A[j + j * ld];
+    for (int c = j + 1 + threadIdx.x; c < k0 + jb; c += blockDim.x) urow[c - k0] = A[j + c * ld];
+    __syncthreads();
     if (!(piv == piv) || isinf(piv)) {
       if (threadIdx.x == 0) atomicOr(flags, 2);
     } else if (piv == (T)0) {
       if (threadIdx.x == 0) atomicOr(flags, 1);
     } else {
       for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
-        const T l = A[i + j * ld] / piv;
+        // the row's panel segment is loaded before any store so the loads overlap
+        const T a = A[i + j * ld];
+        T x[LU_NB];
+#pragma unroll
+        for (int c = 0; c < LU_NB; ++c) x[c] = (c > j - k0 && c < jb) ? A[i + (size_t)(k0 + c) * ld] : (T)0;
+        const T l = a / piv;
         A[i + j * ld] = l;
-        for (int c = j + 1; c < k0 + jb; ++c) A[i + c * ld] -= l * A[j + c * ld];
+#pragma unroll
+        for (int c = 0; c < LU_NB; ++c)
+          if (c > j - k0 && c < jb) A[i + (size_t)(k0 + c) * ld] = x[c] - l * urow[c];
       }
     }
     __syncthreads();
@@ -529,6 +539,15 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask<T>* tasks, const Ge
       __syncthreads();
     }
   }
+  // all loads of C before any store, so they overlap
+  T cv[4][4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int gi = i0 + ty * 4 + r, gj = j0 + tx * 4 + c;
+      cv[r][c] = (tk.beta != (T)0 && gi < tk.m && gj < tk.n) ? tk.C[gi + (size_t)gj * tk.ldc] : (T)0;
+    }
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     const int gj = j0 + tx * 4 + c;
@@ -537,10 +556,7 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask<T>* tasks, const Ge
     for (int r = 0; r < 4; ++r) {
       const int gi = i0 + ty * 4 + r;
       if (gi >= tk.m) continue;
-      T* cp = tk.C + gi + (size_t)gj * tk.ldc;
-      T v = tk.alpha * acc[r][c];
-      if (tk.beta != (T)0) v += tk.beta * *cp;
-      *cp = v;
+      tk.C[gi + (size_t)gj * tk.ldc] = tk.alpha * acc[r][c] + tk.beta * cv[r][c];
     }
   }
 }
@@ -681,7 +697,9 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmTask<float>* tasks, c
     cur_l = nl;
   }
   cp_async_wait<0>();
-  // epilogue: c0 (g, 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1)
+  // epilogue: c0 (g, 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1); all
+  // loads of C before any store, so they overlap
+  float cv[2][4][4];
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
@@ -690,12 +708,17 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmTask<float>* tasks, c
       for (int e = 0; e < 4; ++e) {
         const int gi = i0 + wm + a * 16 + g + ((e >= 2) ? 8 : 0);
         const int gj = j0 + wn + b * 8 + 2 * t4 + (e & 1);
-        if (gi < tk.m && gj < tk.n) {
-          float* cp = tk.C + gi + (size_t)gj * tk.ldc;
-          float v = tk.alpha * acc[a][b][e];
-          if (tk.beta != 0.f) v += tk.beta * *cp;
-          *cp = v;
-        }
+        cv[a][b][e] = (tk.beta != 0.f && gi < tk.m && gj < tk.n) ? tk.C[gi + (size_t)gj * tk.ldc] : 0.f;
+      }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int gi = i0 + wm + a * 16 + g + ((e >= 2) ? 8 : 0);
+        const int gj = j0 + wn + b * 8 + 2 * t4 + (e & 1);
+        if (gi < tk.m && gj < tk.n) tk.C[gi + (size_t)gj * tk.ldc] = tk.alpha * acc[a][b][e] + tk.beta * cv[a][b][e];
       }
 }
 
@@ -877,15 +900,24 @@ __global__ void k_diag_sqrt(const MatRef<T>* mats, T* const* dout, int nmat) {
 
 // ------------------------------------------------------------------ copies
 template <typename T>
-__global__ void k_copy_tiles(const CopyTask<T>* tasks, const CopyTile* tiles) {
+__global__ void __launch_bounds__(256) k_copy_tiles(const CopyTask<T>* tasks, const CopyTile* tiles) {
   __shared__ T tile[32][33];
   const CopyTile ct = tiles[blockIdx.x];
   const CopyTask<T> tk = tasks[ct.task];
   const int r0 = ct.tr * 32, c0 = ct.tc * 32;
   if (!tk.trans) {
-    for (int idx = threadIdx.x; idx < 1024; idx += blockDim.x) {
-      const int r = r0 + (idx & 31), c = c0 + (idx >> 5);
-      if (r < tk.rows && c < tk.cols) tk.dst[r + (size_t)c * tk.ldd] = tk.src[r + (size_t)c * tk.lds];
+    // 256 threads, 4 elements each, all loaded before any store
+    const int r = r0 + (threadIdx.x & 31), cq = c0 + (threadIdx.x >> 5);
+    T v[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int c = cq + 8 * e;
+      v[e] = (r < tk.rows && c < tk.cols) ? tk.src[r + (size_t)c * tk.lds] : T(0);
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int c = cq + 8 * e;
+      if (r < tk.rows && c < tk.cols) tk.dst[r + (size_t)c * tk.ldd] = v[e];
     }
   } else {
     // dst (rows x cols) = src^T, src is cols x rows

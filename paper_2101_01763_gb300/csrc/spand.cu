@@ -33,6 +33,7 @@
 #include "gemv.cuh"
 #include "umma.cuh"
 #include "umma2.cuh"
+#include "umma3.cuh"
 #include "internal.h"
 
 namespace spand {
@@ -244,21 +245,25 @@ static int gemm_mode() {   // 0: tuned, 1: tcgen05, 2: mma.sync
   static const int m = [] {
     const char* v = std::getenv("SPAND_GEMM");
     if (v && std::strcmp(v, "mma") == 0) return 2;
-    if (v && (std::strcmp(v, "umma") == 0 || std::strcmp(v, "umma2") == 0)) return 1;
+    if (v && (std::strcmp(v, "umma") == 0 || std::strcmp(v, "umma2") == 0 || std::strcmp(v, "umma3") == 0))
+      return 1;
     return 0;
   }();
   return m;
 }
 
-// which tcgen05 kernel: the register-staged 128 x 64 one (default) or the
-// cp.async-pipelined 128 x 128 one (SPAND_GEMM=umma2; measured about 2x slower
-// on the leaf-level elimination products, kept for measurement)
-static bool umma_v1() {
-  static const bool v1 = [] {
-    const char* v = std::getenv("SPAND_GEMM");
-    return !(v && std::strcmp(v, "umma2") == 0);
+// which tcgen05 kernel: 1 = the register-staged 128 x 64 one (default),
+// 2 = the cp.async-pipelined 128 x 128 one (SPAND_GEMM=umma2; measured about 2x
+// slower on the leaf-level elimination products, kept for measurement),
+// 3 = the warp-specialised 128 x 64 one (SPAND_GEMM=umma3)
+static int umma_variant() {
+  static const int v = [] {
+    const char* e = std::getenv("SPAND_GEMM");
+    if (e && std::strcmp(e, "umma2") == 0) return 2;
+    if (e && std::strcmp(e, "umma3") == 0) return 3;
+    return 1;
   }();
-  return v1;
+  return v;
 }
 
 // Online tuner for the choice of GEMM kernel (and with it the tile shape).
@@ -401,8 +406,8 @@ static void launch_gemm(DevMem& tmp, const std::vector<GemmTask<T>>& tasks, cons
     }
     if (ntask > 0) umma = gemm_pick(chunks / ntask, flops, e0, e1) == 0;
   }
-  const bool v1 = umma_v1();
-  const int BM = umma ? (v1 ? UM_BM : U2_BM) : 64, BN = umma ? (v1 ? UM_BN : U2_BN) : 64;
+  const int uv = umma_variant();
+  const int BM = umma ? (uv == 2 ? U2_BM : UM_BM) : 64, BN = umma ? (uv == 2 ? U2_BN : UM_BN) : 64;
   std::vector<TileItem> tiles;
   for (int t = 0; t < (int)tasks.size(); ++t) {
     if (tasks[t].m <= 0 || tasks[t].n <= 0) continue;
@@ -432,10 +437,14 @@ static void launch_gemm(DevMem& tmp, const std::vector<GemmTask<T>>& tasks, cons
   } log_at_end{logit, rec, st};
   if constexpr (std::is_same<T, float>::value) {
     if (e0) cudaEventRecord(e0, st);
-    if (umma && v1) {
+    if (umma && uv == 1) {
       static std::atomic<uint64_t> attr{0};
       once_per_device(attr, [] { set_dyn_smem((const void*)k_gemm_umma, UM_SMEM_BYTES); });
       k_gemm_umma<<<(unsigned)tiles.size(), 128, UM_SMEM_BYTES, st>>>(dt, dm, dl);
+    } else if (umma && uv == 3) {
+      static std::atomic<uint64_t> attr3{0};
+      once_per_device(attr3, [] { set_dyn_smem((const void*)k_gemm_umma3, U3_SMEM_BYTES); });
+      k_gemm_umma3<<<(unsigned)tiles.size(), U3_THREADS, U3_SMEM_BYTES, st>>>(dt, dm, dl);
     } else if (umma) {
       static std::atomic<uint64_t> attr2{0};
       once_per_device(attr2, [] { set_dyn_smem((const void*)k_gemm_umma2, U2_SMEM_BYTES); });
@@ -483,9 +492,20 @@ __global__ void __launch_bounds__(256) k_row_perm(const RowPermTask* tasks, cons
   const T* s = static_cast<const T*>(tk.src);
   T* d = static_cast<T*>(tk.dst);
   const int n = tk.rows;
-  for (int idx = threadIdx.x; idx < 64 * 32; idx += blockDim.x) {
-    const int r = tl.r0 + (idx & 63), c = tl.c0 + (idx >> 6);
-    if (r < n && c < tk.cols) d[r + (size_t)c * n] = s[tk.perm[r] + (size_t)c * n];
+  // 8 elements per thread, all loaded before any store so the loads overlap
+  const int r = tl.r0 + (threadIdx.x & 63), cq = tl.c0 + (threadIdx.x >> 6);
+  if (r >= n) return;
+  const int pr = tk.perm[r];
+  T v[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int c = cq + 4 * e;
+    v[e] = (c < tk.cols) ? s[pr + (size_t)c * n] : T(0);
+  }
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int c = cq + 4 * e;
+    if (c < tk.cols) d[r + (size_t)c * n] = v[e];
   }
 }
 

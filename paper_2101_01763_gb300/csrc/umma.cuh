@@ -274,15 +274,16 @@ __global__ void __launch_bounds__(128, 4) k_gemm_umma(const GemmTask<float>* tas
         for (int e = 0; e < 16; ++e) v[e] = 0u;
       }
       if (gi < tk.m) {
+        // all loads of C before any store, so they overlap (a load placed
+        // after a store to C cannot be moved above it by the compiler)
+        float cv[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+          cv[e] = (tk.beta != 0.f && j0 + cb + e < tk.n) ? tk.C[gi + (size_t)(j0 + cb + e) * tk.ldc] : 0.f;
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
           const int gj = j0 + cb + e;
-          if (gj < tk.n) {
-            float* cp = tk.C + gi + (size_t)gj * tk.ldc;
-            float val = tk.alpha * __uint_as_float(v[e]);
-            if (tk.beta != 0.f) val += tk.beta * *cp;
-            *cp = val;
-          }
+          if (gj < tk.n) tk.C[gi + (size_t)gj * tk.ldc] = tk.alpha * __uint_as_float(v[e]) + tk.beta * cv[e];
         }
       }
     }
