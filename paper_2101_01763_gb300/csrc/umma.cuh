@@ -110,53 +110,74 @@ __global__ void __launch_bounds__(128, 4) k_gemm_umma(const GemmTask<float>* tas
   while (cur_t < tk.t1 && term_klim(terms[cur_t], i0, j0, UM_BM, UM_BN) <= 0) ++cur_t;
   int item = 0;
   bool failed = false;
-  // operand values of one k-chunk held in registers: this thread's A row (UM_BK k)
-  // and half of one B column (UM_BH k).  The loads of chunk i+1 are issued right
-  // after the MMAs of chunk i, so their latency overlaps the tensor-core work.
-  const int r = tid, gi = i0 + r;
-  const int c = tid & 63, half = tid >> 6, gj = j0 + c;
+  // operand values of one k-chunk held in registers as pieces of 4 consecutive
+  // k of one row: 4 pieces of op(A) (128 x UM_BK) and 2 of op(B)^T (64 x UM_BK).
+  // An operand stored along k is read 8 rows x 64 bytes per warp instruction
+  // (piece q of lane l: row kr + 32 q, k offset kk); one stored along m (n)
+  // keeps a row (column) per thread and reads its k values one at a time, 32
+  // consecutive rows per warp instruction.  The loads of chunk i+1 are issued
+  // right after the MMAs of chunk i, so their latency overlaps the tensor-core
+  // work.
+  const int kr = 8 * warp + (lane & 7), kk = 4 * (lane >> 3);
+  const int c = tid & 63, half = tid >> 6;
   float x[UM_BK], y[UM_BH];
+  bool a_kc = false, b_kc = false;      // layout of the chunk held in x / y
   auto load_chunk = [&](int t_, int l_) {
     const GemmTerm<float> tm = terms[t_];
-    const bool a_vec = tm.ta && ((tm.lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(tm.A) & 15) == 0) &&
-                       l_ + UM_BK <= tm.k;
-    if (a_vec && gi < tk.m) {
-      const float4* src = reinterpret_cast<const float4*>(tm.A + l_ + (size_t)gi * tm.lda);
+    a_kc = tm.ta != 0;
+    b_kc = tm.tb == 0;
+    if (a_kc) {
+      const int gl = l_ + kk;
+      const bool vec = ((tm.lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(tm.A) & 15) == 0) && gl + 4 <= tm.k;
 #pragma unroll
-      for (int q = 0; q < UM_BK / 4; ++q) {
-        const float4 f = src[q];
-        x[4 * q] = f.x;
-        x[4 * q + 1] = f.y;
-        x[4 * q + 2] = f.z;
-        x[4 * q + 3] = f.w;
+      for (int q = 0; q < 4; ++q) {
+        const int gi = i0 + kr + 32 * q;
+        if (vec) {
+          const float4 f = gi < tk.m ? *reinterpret_cast<const float4*>(tm.A + gl + (size_t)gi * tm.lda)
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+          x[4 * q] = f.x;
+          x[4 * q + 1] = f.y;
+          x[4 * q + 2] = f.z;
+          x[4 * q + 3] = f.w;
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            x[4 * q + e] = (gi < tk.m && gl + e < tm.k) ? tm.A[gl + e + (size_t)gi * tm.lda] : 0.f;
+        }
       }
     } else {
+      const int gi = i0 + tid;
 #pragma unroll
       for (int e = 0; e < UM_BK; ++e) {
         const int gl = l_ + e;
-        x[e] = (gi < tk.m && gl < tm.k) ? (tm.ta ? tm.A[gl + (size_t)gi * tm.lda] : tm.A[gi + (size_t)gl * tm.lda])
-                                        : 0.f;
+        x[e] = (gi < tk.m && gl < tm.k) ? tm.A[gi + (size_t)gl * tm.lda] : 0.f;
       }
     }
-    const int kb = l_ + half * UM_BH;
-    const bool b_vec = !tm.tb && ((tm.ldb & 3) == 0) && ((reinterpret_cast<uintptr_t>(tm.B) & 15) == 0) &&
-                       kb + UM_BH <= tm.k;
-    if (b_vec && gj < tk.n) {
-      const float4* src = reinterpret_cast<const float4*>(tm.B + kb + (size_t)gj * tm.ldb);
+    if (b_kc) {
+      const int gl = l_ + kk;
+      const bool vec = ((tm.ldb & 3) == 0) && ((reinterpret_cast<uintptr_t>(tm.B) & 15) == 0) && gl + 4 <= tm.k;
 #pragma unroll
-      for (int q = 0; q < UM_BH / 4; ++q) {
-        const float4 f = src[q];
-        y[4 * q] = f.x;
-        y[4 * q + 1] = f.y;
-        y[4 * q + 2] = f.z;
-        y[4 * q + 3] = f.w;
+      for (int q = 0; q < 2; ++q) {
+        const int gj = j0 + kr + 32 * q;
+        if (vec) {
+          const float4 f = gj < tk.n ? *reinterpret_cast<const float4*>(tm.B + gl + (size_t)gj * tm.ldb)
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+          y[4 * q] = f.x;
+          y[4 * q + 1] = f.y;
+          y[4 * q + 2] = f.z;
+          y[4 * q + 3] = f.w;
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            y[4 * q + e] = (gj < tk.n && gl + e < tm.k) ? tm.B[gl + e + (size_t)gj * tm.ldb] : 0.f;
+        }
       }
     } else {
+      const int gj = j0 + c, kb = l_ + half * UM_BH;
 #pragma unroll
       for (int e = 0; e < UM_BH; ++e) {
         const int gl = kb + e;
-        y[e] = (gj < tk.n && gl < tm.k) ? (tm.tb ? tm.B[gj + (size_t)gl * tm.ldb] : tm.B[gl + (size_t)gj * tm.ldb])
-                                        : 0.f;
+        y[e] = (gj < tk.n && gl < tm.k) ? tm.B[gj + (size_t)gl * tm.ldb] : 0.f;
       }
     }
   };
@@ -186,7 +207,7 @@ __global__ void __launch_bounds__(128, 4) k_gemm_umma(const GemmTask<float>* tas
         lo.y = to_tf32(x[kq + 1] - __uint_as_float(hi.y));
         lo.z = to_tf32(x[kq + 2] - __uint_as_float(hi.z));
         lo.w = to_tf32(x[kq + 3] - __uint_as_float(hi.w));
-        const uint32_t off = umma_off_bk(r, kq);
+        const uint32_t off = a_kc ? umma_off_bk(kr + 8 * kq, kk) : umma_off_bk(tid, kq);   // piece kq / 4
         *reinterpret_cast<uint4*>(st + off) = hi;
         *reinterpret_cast<uint4*>(st + UM_A_BYTES + off) = lo;
       }
@@ -201,7 +222,7 @@ __global__ void __launch_bounds__(128, 4) k_gemm_umma(const GemmTask<float>* tas
         lo.y = to_tf32(y[kq + 1] - __uint_as_float(hi.y));
         lo.z = to_tf32(y[kq + 2] - __uint_as_float(hi.z));
         lo.w = to_tf32(y[kq + 3] - __uint_as_float(hi.w));
-        const uint32_t off = umma_off_bk(c, half * UM_BH + kq);
+        const uint32_t off = b_kc ? umma_off_bk(kr + 8 * kq, kk) : umma_off_bk(c, half * UM_BH + kq);
         *reinterpret_cast<uint4*>(st + 2 * UM_A_BYTES + off) = hi;
         *reinterpret_cast<uint4*>(st + 2 * UM_A_BYTES + UM_B_BYTES + off) = lo;
       }
