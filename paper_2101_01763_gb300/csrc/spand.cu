@@ -266,6 +266,15 @@ static int umma_variant() {
   return v;
 }
 
+// register sets of operand prefetch in k_gemm_umma (SPAND_GEMM_DEPTH=1 or 2)
+static int umma_depth() {
+  static const int d = [] {
+    const char* e = std::getenv("SPAND_GEMM_DEPTH");
+    return (e && e[0] == '2') ? 2 : 1;
+  }();
+  return d;
+}
+
 // Online tuner for the choice of GEMM kernel (and with it the tile shape).
 // Launches are grouped by device, the average number of 32-wide k-chunks per
 // product (log2 bucket) and the logical flop count (log2 bucket).  The first
@@ -353,7 +362,9 @@ static int gemm_pick(double avg_chunks, double flops, cudaEvent_t& e0, cudaEvent
 }
 
 // SPAND_DEBUG=3: CUDA-event time, logical flops and kernel of every grouped
-// GEMM launch, summed per purpose (tag) and printed when the factorization ends
+// GEMM launch, summed per purpose (tag) and printed when the factorization ends;
+// SPAND_DEBUG=4 also prints every launch in order (index among the launches of
+// its kernel, tag, tiles, time)
 struct GemmLog {
   struct Rec {
     const char* tag;
@@ -369,9 +380,14 @@ struct GemmLog {
   }
   void print_and_clear() {
     std::map<std::string, std::array<double, 4>> agg;   // ms, flops, launches, tiles
+    int nk[3] = {0, 0, 0};
     for (auto& r : recs) {
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) cudaGetLastError();
+      if (debug_level() >= 4)
+        std::fprintf(stderr, "spand: GEMM launch %s #%d %-14s %8zu tiles %9.3f ms %7.1f TFLOP/s\n",
+                     r.kind == 0 ? "tcgen05" : r.kind == 1 ? "mma.sync" : "fp64", nk[r.kind]++, r.tag, r.tiles, ms,
+                     ms > 0 ? r.flops / (ms * 1e9) : 0.0);
       auto& a = agg[std::string(r.tag) + (r.kind == 0 ? " tcgen05" : r.kind == 1 ? " mma.sync" : " fp64")];
       a[0] += ms;
       a[1] += r.flops;
@@ -426,7 +442,8 @@ static void launch_gemm(DevMem& tmp, const std::vector<GemmTask<T>>& tasks, cons
                      cudaEventCreate(&rec.b) == cudaSuccess && cudaEventRecord(rec.a, st) == cudaSuccess;
   if (logit)
     for (const auto& tk : tasks)
-      for (int t = tk.t0; t < tk.t1; ++t) rec.flops += 2.0 * tk.m * (double)tk.n * terms[t].k;
+      for (int t = tk.t0; t < tk.t1; ++t)   // a triangular operand halves the useful flops
+        rec.flops += (terms[t].tri ? 1.0 : 2.0) * tk.m * (double)tk.n * terms[t].k;
   struct LogAtEnd {
     bool on;
     GemmLog::Rec& r;
@@ -437,10 +454,14 @@ static void launch_gemm(DevMem& tmp, const std::vector<GemmTask<T>>& tasks, cons
   } log_at_end{logit, rec, st};
   if constexpr (std::is_same<T, float>::value) {
     if (e0) cudaEventRecord(e0, st);
-    if (umma && uv == 1) {
+    if (umma && uv == 1 && umma_depth() == 2) {
       static std::atomic<uint64_t> attr{0};
-      once_per_device(attr, [] { set_dyn_smem((const void*)k_gemm_umma, UM_SMEM_BYTES); });
-      k_gemm_umma<<<(unsigned)tiles.size(), 128, UM_SMEM_BYTES, st>>>(dt, dm, dl);
+      once_per_device(attr, [] { set_dyn_smem((const void*)k_gemm_umma<2>, UM_SMEM_BYTES); });
+      k_gemm_umma<2><<<(unsigned)tiles.size(), 128, UM_SMEM_BYTES, st>>>(dt, dm, dl);
+    } else if (umma && uv == 1) {
+      static std::atomic<uint64_t> attr1{0};
+      once_per_device(attr1, [] { set_dyn_smem((const void*)k_gemm_umma<1>, UM_SMEM_BYTES); });
+      k_gemm_umma<1><<<(unsigned)tiles.size(), 128, UM_SMEM_BYTES, st>>>(dt, dm, dl);
     } else if (umma && uv == 3) {
       static std::atomic<uint64_t> attr3{0};
       once_per_device(attr3, [] { set_dyn_smem((const void*)k_gemm_umma3, U3_SMEM_BYTES); });
@@ -1338,6 +1359,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       }
       if (tmp.err || pm.err) return SPAND_ERR_NOMEM;
       launch_row_perm(tmp, ps, pd, pp, pr_, pc_, st);
+      // triangular-times-dense products: m n k useful flops each (half of a full product)
       double gflops = 0;
       for (size_t q = 0; q < tasks.size(); ++q) gflops += 1.0 * tasks[q].m * (double)tasks[q].n * terms[q].k;
       ev_begin(ev_gm[l]);

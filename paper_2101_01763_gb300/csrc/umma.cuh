@@ -2,10 +2,11 @@
 //
 // Same task / term / tile contract as k_gemm_tc (C = alpha * sum_t op(A_t) op(B_t)
 // + beta * C, column-major), on 128 x 64 output tiles:
-//  * 128 threads stage one 32-wide k-chunk of op(A) (128 x 32) and op(B)^T
-//    (64 x 32) in shared memory, split into TF32 high parts and TF32
-//    remainders, in the K-major "core matrix" layout the MMA reads without
-//    swizzling (8 rows x 16 bytes per core matrix);
+//  * 128 threads stage one 16-wide k-chunk of op(A) (128 x 16) and op(B)^T
+//    (64 x 16) in shared memory, split into TF32 high parts (rounded) and the
+//    exact FP32 remainders (of which the tensor core reads the top 19 bits),
+//    in the K-major "core matrix" layout the MMA reads without swizzling
+//    (8 rows x 16 bytes per core matrix);
 //  * one thread issues tcgen05.mma.kind::tf32 with the accumulator in tensor
 //    memory (128 lanes x 64 FP32 columns): hi*lo + lo*hi + hi*hi per 8-wide
 //    k-step (error-compensated 3xTF32, about FP32 accuracy), and commits the
@@ -76,6 +77,7 @@ __device__ inline bool mbar_wait(uint32_t bar, uint32_t parity) {
 
 __device__ int g_umma_fail;   // set when an MMA completion wait ran out of time
 
+template <int DEPTH>
 __global__ void __launch_bounds__(128, 4) k_gemm_umma(const GemmTask<float>* tasks, const GemmTerm<float>* terms,
                                                       const TileItem* tiles) {
   extern __shared__ unsigned char um_raw[];
@@ -105,9 +107,22 @@ __global__ void __launch_bounds__(128, 4) k_gemm_umma(const GemmTask<float>* tas
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
 
-  // flattened (term, k-chunk) sequence, as in k_gemm_tc
-  int cur_t = tk.t0, cur_l = 0;
-  while (cur_t < tk.t1 && term_klim(terms[cur_t], i0, j0, UM_BM, UM_BN) <= 0) ++cur_t;
+  // flattened (term, k-chunk) sequence, as in k_gemm_tc: nch chunks in all;
+  // (pf_t, pf_l) is the next chunk to load
+  int nch = 0;
+  for (int t = tk.t0; t < tk.t1; ++t) {
+    const int kl = term_klim(terms[t], i0, j0, UM_BM, UM_BN);
+    if (kl > 0) nch += (kl + UM_BK - 1) / UM_BK;
+  }
+  int pf_t = tk.t0, pf_l = 0;
+  while (pf_t < tk.t1 && term_klim(terms[pf_t], i0, j0, UM_BM, UM_BN) <= 0) ++pf_t;
+  auto advance = [&]() {
+    pf_l += UM_BK;
+    while (pf_t < tk.t1 && pf_l >= term_klim(terms[pf_t], i0, j0, UM_BM, UM_BN)) {
+      ++pf_t;
+      pf_l = 0;
+    }
+  };
   int item = 0;
   bool failed = false;
   // operand values of one k-chunk held in registers as pieces of 4 consecutive
@@ -115,14 +130,12 @@ __global__ void __launch_bounds__(128, 4) k_gemm_umma(const GemmTask<float>* tas
   // An operand stored along k is read 8 rows x 64 bytes per warp instruction
   // (piece q of lane l: row kr + 32 q, k offset kk); one stored along m (n)
   // keeps a row (column) per thread and reads its k values one at a time, 32
-  // consecutive rows per warp instruction.  The loads of chunk i+1 are issued
-  // right after the MMAs of chunk i, so their latency overlaps the tensor-core
-  // work.
+  // consecutive rows per warp instruction.  DEPTH register sets: the loads of
+  // chunk i + DEPTH are issued right after the MMAs of chunk i, so their
+  // latency overlaps the staging and tensor-core work of DEPTH chunks.
   const int kr = 8 * warp + (lane & 7), kk = 4 * (lane >> 3);
   const int c = tid & 63, half = tid >> 6;
-  float x[UM_BK], y[UM_BH];
-  bool a_kc = false, b_kc = false;      // layout of the chunk held in x / y
-  auto load_chunk = [&](int t_, int l_) {
+  auto load_chunk = [&](int t_, int l_, float (&x)[UM_BK], float (&y)[UM_BH], bool& a_kc, bool& b_kc) {
     const GemmTerm<float> tm = terms[t_];
     a_kc = tm.ta != 0;
     b_kc = tm.tb == 0;
@@ -147,11 +160,10 @@ __global__ void __launch_bounds__(128, 4) k_gemm_umma(const GemmTask<float>* tas
       }
     } else {
       const int gi = i0 + tid;
+      const float* pa = tm.A + gi + (size_t)l_ * tm.lda;
+      const int nk = gi < tk.m ? tm.k - l_ : 0;     // k values left in this row
 #pragma unroll
-      for (int e = 0; e < UM_BK; ++e) {
-        const int gl = l_ + e;
-        x[e] = (gi < tk.m && gl < tm.k) ? tm.A[gi + (size_t)gl * tm.lda] : 0.f;
-      }
+      for (int e = 0; e < UM_BK; ++e) x[e] = e < nk ? pa[e * tm.lda] : 0.f;
     }
     if (b_kc) {
       const int gl = l_ + kk;
@@ -174,25 +186,21 @@ __global__ void __launch_bounds__(128, 4) k_gemm_umma(const GemmTask<float>* tas
       }
     } else {
       const int gj = j0 + c, kb = l_ + half * UM_BH;
+      const float* pb = tm.B + gj + (size_t)kb * tm.ldb;
+      const int nk = gj < tk.n ? tm.k - kb : 0;
 #pragma unroll
-      for (int e = 0; e < UM_BH; ++e) {
-        const int gl = kb + e;
-        y[e] = (gj < tk.n && gl < tm.k) ? tm.B[gj + (size_t)gl * tm.ldb] : 0.f;
-      }
+      for (int e = 0; e < UM_BH; ++e) y[e] = e < nk ? pb[e * tm.ldb] : 0.f;
     }
   };
-  if (cur_t < tk.t1) load_chunk(cur_t, cur_l);
-  while (cur_t < tk.t1) {
+  // stage chunk `item` from registers and issue its MMAs; false on a timed-out wait
+  auto process = [&](const float (&x)[UM_BK], const float (&y)[UM_BH], bool a_kc, bool b_kc) -> bool {
     const int s = item & 1;
     unsigned char* st = um + s * UM_STAGE_BYTES;
     if (item >= 2) {
-      // the MMAs that read this stage two chunks ago must be done (the outcome
-      // is made uniform over the CTA so every thread leaves the loop together)
-      const bool ok = mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((item >> 1) - 1) & 1));
-      if (__syncthreads_or(!ok)) {
-        failed = true;
-        break;
-      }
+      // the MMAs that read this stage two chunks ago must be done; one thread
+      // polls, the others wait at the barrier, and the outcome is uniform
+      const bool ok = tid != 0 || mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((item >> 1) - 1) & 1));
+      if (__syncthreads_or(!ok)) return false;
     }
     // ---- split the chunk's values into TF32 hi / lo in the core-matrix layout
     {
@@ -203,10 +211,10 @@ __global__ void __launch_bounds__(128, 4) k_gemm_umma(const GemmTask<float>* tas
         hi.y = to_tf32(x[kq + 1]);
         hi.z = to_tf32(x[kq + 2]);
         hi.w = to_tf32(x[kq + 3]);
-        lo.x = to_tf32(x[kq] - __uint_as_float(hi.x));
-        lo.y = to_tf32(x[kq + 1] - __uint_as_float(hi.y));
-        lo.z = to_tf32(x[kq + 2] - __uint_as_float(hi.z));
-        lo.w = to_tf32(x[kq + 3] - __uint_as_float(hi.w));
+        lo.x = __float_as_uint(x[kq] - __uint_as_float(hi.x));
+        lo.y = __float_as_uint(x[kq + 1] - __uint_as_float(hi.y));
+        lo.z = __float_as_uint(x[kq + 2] - __uint_as_float(hi.z));
+        lo.w = __float_as_uint(x[kq + 3] - __uint_as_float(hi.w));
         const uint32_t off = a_kc ? umma_off_bk(kr + 8 * kq, kk) : umma_off_bk(tid, kq);   // piece kq / 4
         *reinterpret_cast<uint4*>(st + off) = hi;
         *reinterpret_cast<uint4*>(st + UM_A_BYTES + off) = lo;
@@ -218,10 +226,10 @@ __global__ void __launch_bounds__(128, 4) k_gemm_umma(const GemmTask<float>* tas
         hi.y = to_tf32(y[kq + 1]);
         hi.z = to_tf32(y[kq + 2]);
         hi.w = to_tf32(y[kq + 3]);
-        lo.x = to_tf32(y[kq] - __uint_as_float(hi.x));
-        lo.y = to_tf32(y[kq + 1] - __uint_as_float(hi.y));
-        lo.z = to_tf32(y[kq + 2] - __uint_as_float(hi.z));
-        lo.w = to_tf32(y[kq + 3] - __uint_as_float(hi.w));
+        lo.x = __float_as_uint(y[kq] - __uint_as_float(hi.x));
+        lo.y = __float_as_uint(y[kq + 1] - __uint_as_float(hi.y));
+        lo.z = __float_as_uint(y[kq + 2] - __uint_as_float(hi.z));
+        lo.w = __float_as_uint(y[kq + 3] - __uint_as_float(hi.w));
         const uint32_t off = b_kc ? umma_off_bk(kr + 8 * kq, kk) : umma_off_bk(c, half * UM_BH + kq);
         *reinterpret_cast<uint4*>(st + 2 * UM_A_BYTES + off) = hi;
         *reinterpret_cast<uint4*>(st + 2 * UM_A_BYTES + UM_B_BYTES + off) = lo;
@@ -258,15 +266,39 @@ __global__ void __launch_bounds__(128, 4) k_gemm_umma(const GemmTask<float>* tas
           smem_u32(&mbar[s])));
     }
     ++item;
-    cur_l += UM_BK;
-    while (cur_t < tk.t1 && cur_l >= term_klim(terms[cur_t], i0, j0, UM_BM, UM_BN)) {
-      ++cur_t;
-      cur_l = 0;
+    return true;
+  };
+  float x0[UM_BK], y0[UM_BH], x1[UM_BK], y1[UM_BH];
+  bool ak0 = false, bk0 = false, ak1 = false, bk1 = false;
+  if (pf_t < tk.t1) {
+    load_chunk(pf_t, pf_l, x0, y0, ak0, bk0);
+    advance();
+  }
+  if (DEPTH == 2 && pf_t < tk.t1) {
+    load_chunk(pf_t, pf_l, x1, y1, ak1, bk1);
+    advance();
+  }
+  while (item < nch) {
+    if (!process(x0, y0, ak0, bk0)) {
+      failed = true;
+      break;
     }
-    if (cur_t < tk.t1) load_chunk(cur_t, cur_l);   // overlaps the MMAs just issued
+    if (pf_t < tk.t1) {      // overlaps the MMAs just issued
+      load_chunk(pf_t, pf_l, x0, y0, ak0, bk0);
+      advance();
+    }
+    if (DEPTH == 1 || item >= nch) continue;
+    if (!process(x1, y1, ak1, bk1)) {
+      failed = true;
+      break;
+    }
+    if (pf_t < tk.t1) {
+      load_chunk(pf_t, pf_l, x1, y1, ak1, bk1);
+      advance();
+    }
   }
   // ---- wait for the last committed chunk (it tracks every earlier MMA of the thread)
-  if (item > 0 && !failed) {
+  if (tid == 0 && item > 0 && !failed) {
     const int last = item - 1;
     if (!mbar_wait(smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1))) failed = true;
   }
