@@ -114,13 +114,25 @@ __global__ void __launch_bounds__(128, 4) k_gemm_umma(const GemmTask<float>* tas
     const int kl = term_klim(terms[t], i0, j0, UM_BM, UM_BN);
     if (kl > 0) nch += (kl + UM_BK - 1) / UM_BK;
   }
+  // the term being loaded stays in registers (ct, its k limit ct_kl): a
+  // global load of the term per chunk would put its latency on every chunk
   int pf_t = tk.t0, pf_l = 0;
-  while (pf_t < tk.t1 && term_klim(terms[pf_t], i0, j0, UM_BM, UM_BN) <= 0) ++pf_t;
+  GemmTerm<float> ct{};
+  int ct_kl = 0;
+  auto seek = [&]() {     // first term from pf_t on with a non-empty k range
+    for (; pf_t < tk.t1; ++pf_t) {
+      ct = terms[pf_t];
+      ct_kl = term_klim(ct, i0, j0, UM_BM, UM_BN);
+      if (ct_kl > 0) break;
+    }
+  };
+  seek();
   auto advance = [&]() {
     pf_l += UM_BK;
-    while (pf_t < tk.t1 && pf_l >= term_klim(terms[pf_t], i0, j0, UM_BM, UM_BN)) {
-      ++pf_t;
+    if (pf_l >= ct_kl) {
       pf_l = 0;
+      ++pf_t;
+      seek();
     }
   };
   int item = 0;
@@ -135,8 +147,9 @@ __global__ void __launch_bounds__(128, 4) k_gemm_umma(const GemmTask<float>* tas
   // latency overlaps the staging and tensor-core work of DEPTH chunks.
   const int kr = 8 * warp + (lane & 7), kk = 4 * (lane >> 3);
   const int c = tid & 63, half = tid >> 6;
-  auto load_chunk = [&](int t_, int l_, float (&x)[UM_BK], float (&y)[UM_BH], bool& a_kc, bool& b_kc) {
-    const GemmTerm<float> tm = terms[t_];
+  const uint64_t desc0 = umma_desc(smem_u32(um), 128, UM_SBO), desc1 = umma_desc(smem_u32(um + UM_STAGE_BYTES), 128, UM_SBO);
+  auto load_chunk = [&](int l_, float (&x)[UM_BK], float (&y)[UM_BH], bool& a_kc, bool& b_kc) {
+    const GemmTerm<float>& tm = ct;
     a_kc = tm.ta != 0;
     b_kc = tm.tb == 0;
     if (a_kc) {
@@ -240,14 +253,15 @@ __global__ void __launch_bounds__(128, 4) k_gemm_umma(const GemmTask<float>* tas
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t a_hi = smem_u32(st), a_lo = a_hi + UM_A_BYTES;
-      const uint32_t b_hi = a_hi + 2 * UM_A_BYTES, b_lo = b_hi + UM_B_BYTES;
       const uint32_t idesc = umma_idesc_tf32();
+      const uint64_t d0 = s ? desc1 : desc0;   // descriptor of the stage's A hi part
 #pragma unroll
       for (int ks = 0; ks < UM_BK / 8; ++ks) {
-        const uint32_t ko = ks * 256;            // two core matrices along K per 8-wide step
-        const uint64_t dah = umma_desc(a_hi + ko, 128, UM_SBO), dal = umma_desc(a_lo + ko, 128, UM_SBO);
-        const uint64_t dbh = umma_desc(b_hi + ko, 128, UM_SBO), dbl = umma_desc(b_lo + ko, 128, UM_SBO);
+        // two core matrices along K (256 bytes) per 8-wide step; descriptor
+        // addresses are in 16-byte units in the low bits
+        const uint64_t ko = (uint64_t)(ks * 256) >> 4;
+        const uint64_t dah = d0 + ko, dal = d0 + ko + (UM_A_BYTES >> 4);
+        const uint64_t dbh = d0 + ko + ((2 * UM_A_BYTES) >> 4), dbl = d0 + ko + ((2 * UM_A_BYTES + UM_B_BYTES) >> 4);
         const uint32_t acc0 = (item > 0 || ks > 0) ? 1u : 0u;
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
@@ -271,11 +285,11 @@ __global__ void __launch_bounds__(128, 4) k_gemm_umma(const GemmTask<float>* tas
   float x0[UM_BK], y0[UM_BH], x1[UM_BK], y1[UM_BH];
   bool ak0 = false, bk0 = false, ak1 = false, bk1 = false;
   if (pf_t < tk.t1) {
-    load_chunk(pf_t, pf_l, x0, y0, ak0, bk0);
+    load_chunk(pf_l, x0, y0, ak0, bk0);
     advance();
   }
   if (DEPTH == 2 && pf_t < tk.t1) {
-    load_chunk(pf_t, pf_l, x1, y1, ak1, bk1);
+    load_chunk(pf_l, x1, y1, ak1, bk1);
     advance();
   }
   while (item < nch) {
@@ -284,7 +298,7 @@ __global__ void __launch_bounds__(128, 4) k_gemm_umma(const GemmTask<float>* tas
       break;
     }
     if (pf_t < tk.t1) {      // overlaps the MMAs just issued
-      load_chunk(pf_t, pf_l, x0, y0, ak0, bk0);
+      load_chunk(pf_l, x0, y0, ak0, bk0);
       advance();
     }
     if (DEPTH == 1 || item >= nch) continue;
@@ -293,7 +307,7 @@ __global__ void __launch_bounds__(128, 4) k_gemm_umma(const GemmTask<float>* tas
       break;
     }
     if (pf_t < tk.t1) {
-      load_chunk(pf_t, pf_l, x1, y1, ak1, bk1);
+      load_chunk(pf_l, x1, y1, ak1, bk1);
       advance();
     }
   }
