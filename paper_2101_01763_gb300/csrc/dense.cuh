@@ -938,13 +938,19 @@ template <typename T>
 struct EyeTask {
   T* dst;
   int ldd, r;
+  int rows;        // 0: write the r diagonal ones only; else write all rows x r entries ([I_r; 0])
 };
 
 template <typename T>
 __global__ void k_eye(const EyeTask<T>* tasks, int ntask) {
   for (int t = blockIdx.x; t < ntask; t += gridDim.x) {
     const EyeTask<T> tk = tasks[t];
-    for (int i = threadIdx.x; i < tk.r; i += blockDim.x) tk.dst[i + (size_t)i * tk.ldd] = (T)1;
+    if (tk.rows == 0) {
+      for (int i = threadIdx.x; i < tk.r; i += blockDim.x) tk.dst[i + (size_t)i * tk.ldd] = (T)1;
+    } else {
+      for (int j = 0; j < tk.r; ++j)
+        for (int i = threadIdx.x; i < tk.rows; i += blockDim.x) tk.dst[i + (size_t)j * tk.ldd] = (T)(i == j);
+    }
   }
 }
 

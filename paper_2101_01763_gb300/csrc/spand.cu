@@ -1121,6 +1121,16 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
     t_mark = t;
   };
 
+  // SPAND_DEBUG=2: host time between named points of the level loop, summed
+  // over levels and printed at the end (where the host, not the GPU, is busy)
+  std::map<std::string, double> host_ticks;
+  double t_tick = t_begin;
+  auto tick = [&](const char* what) {
+    if (debug_level() < 2) return;
+    const double t = now_ms();
+    host_ticks[what] += t - t_tick;
+    t_tick = t;
+  };
   auto sync_st = [&]() -> cudaError_t {
     const double t0 = now_ms();
     const cudaError_t e = cudaStreamSynchronize(st);
@@ -1295,6 +1305,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
     for (auto& pr : L.pattern)
       if (pr.first != pr.second) nbr[pr.first].push_back(pr.second);
     mark(0);
+    tick("a nbr lists (and level start)");
     // ================= 1. eliminate interiors (Eq. 10)
     std::vector<int> I;
     for (int c = 0; c < nc; ++c)
@@ -1398,6 +1409,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       break;
     }
     mark(1);
+    tick("b eliminate interiors");
     // ================= 2. scale interfaces (Eq. 11)
     std::vector<int> Fc;
     for (int c = 0; c < nc; ++c)
@@ -1464,6 +1476,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       launch_gemm(tmp, t2, m2, st, "scale");
     }
     mark(2);
+    tick("c scale interfaces");
     // ================= 3. all Q first (Eq. 12): RRQR of [A_sn A_ns^T]
     std::vector<QrTask<T>> qt;
     std::vector<int> qcl;
@@ -1887,10 +1900,12 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       }
     }
     mark(3);
+    tick("d RRQR setup, launch, D2H of streamed work");
     int hflags[4];
     SPAND_CUDA_TRY(cudaMemcpyAsync(hflags, d_flags, sizeof(hflags), cudaMemcpyDeviceToHost, st));
     SPAND_CUDA_TRY(sync_st());
     mark(4);
+    tick("e sync after RRQR");
     if (hflags[0] & 1) return SPAND_ERR_ZERO_PIVOT;   // the root cause when both are set
     if (hflags[0] & 2) return SPAND_ERR_NONFINITE;
     if (hflags[0] & 16) {
@@ -1960,6 +1975,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       Sq.max_r[l] = std::max<int64_t>(Sq.max_r[l], rank[q]);
     }
     if (pm.err) return SPAND_ERR_NOMEM;
+    tick("f ranks, stats, Q_c allocation");
     if (!qt.empty()) {
       // Q_c = [I_r; 0] - V M with M = T V_top^T (compact WY); G = V^T V first
       std::vector<GemmTask<T>> gt, mt, qtk;
@@ -1988,12 +2004,12 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
         nod.push_back(nullptr);
         mm.push_back({Tm, qt[q].V, r, nn, r, 0, 1, 0});
         mt.push_back({M, r, r, r, (T)1, (T)0, (int)mm.size() - 1, (int)mm.size()});
-        SPAND_CUDA_TRY(cudaMemsetAsync(qt[q].Q, 0, sizeof(T) * (size_t)nn * r, st));
-        eye_q.push_back({qt[q].Q, nn, r});
+        eye_q.push_back({qt[q].Q, nn, r, nn});     // Q_c = [I_r; 0] before the update below
         qm.push_back({qt[q].V, M, nn, r, r, 0, 0, 0});
         qtk.push_back({qt[q].Q, nn, nn, r, (T)-1, (T)1, (int)qm.size() - 1, (int)qm.size()});
       }
       if (tmp.err) return SPAND_ERR_NOMEM;
+      tick("g WY task lists");
       launch_gemm(tmp, gt, gm, st, "wy");
       if (!wy.empty()) {
         auto* dw = tmp.upload(wy);
@@ -2003,7 +2019,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
         batched_upper_inverse(tmp, tri, Tinv, st);
         auto* de = tmp.upload(eye_q);
         note_launch();
-        k_eye<T><<<std::min<unsigned>((unsigned)eye_q.size(), 1024), 128, 0, st>>>(de, (int)eye_q.size());
+        k_eye<T><<<std::min<unsigned>((unsigned)eye_q.size(), 4096), 256, 0, st>>>(de, (int)eye_q.size());
       }
       launch_gemm(tmp, mt, mm, st, "wy");
       launch_gemm(tmp, qtk, qm, st, "wy");
@@ -2029,6 +2045,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       R.fa.push_back(f);
     }
     mark(5);
+    tick("h WY launches, apply records");
     // ================= 4. next level: sizes, slots, merged blocks
     const LevelInfo& L2 = P.lv[l + 1];
     const int nc2 = (int)L2.cl.size();
@@ -2051,6 +2068,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
     std::map<std::pair<int, int>, size_t> old_off = boff;
     SPAND_TRY(layout(L2, n2, lvmem2));
     auto oblk = [&](int a, int b) -> T* { return old_arena + old_off.at({a, b}); };
+    tick("i next-level sizes, slots, layout");
     std::vector<EyeTask<T>> eyes;
     std::vector<GemmTask<T>> t1, t2;
     std::vector<GemmTerm<T>> m1, m2;
@@ -2060,7 +2078,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       const int pa = parent[a], pb = parent[b];
       T* dst = blk(pa, pb) + off[a] + (size_t)off[b] * n2[pa];
       if (a == b) {
-        eyes.push_back({dst, n2[pa], r[a]});
+        eyes.push_back({dst, n2[pa], r[a], 0});
         continue;
       }
       // both are sparsified (they have neighbours).  First (Q_ac^T A_ab)^T =
@@ -2074,6 +2092,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       flops += 2.0 * n[a] * (double)n[b] * (r[a] + r[b]);
     }
     if (tmp.err) return SPAND_ERR_NOMEM;
+    tick("j compress task lists");
     launch_gemm(tmp, t1, m1, st, "compress");
     launch_gemm(tmp, t2, m2, st, "compress");
     if (!eyes.empty()) {
@@ -2088,6 +2107,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
     lvmem2.ptrs.clear();
     n = n2;
     slots = slots2;
+    tick("k compress launches, frees");
   }
   lvmem.free_all();
   {
@@ -2108,6 +2128,8 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
   }
   S.factor_flops = flops;
   if (debug_level() >= 3) GemmLog::get().print_and_clear();
+  tick("l final sync");
+  for (auto& kv : host_ticks) std::fprintf(stderr, "spand: host %-46s %9.2f ms\n", kv.first.c_str(), kv.second);
 
   mark(6);
   // ================= apply program
