@@ -236,6 +236,42 @@ __global__ void __launch_bounds__(256) k_getrf_panel(const MatRef<T>* mats, int 
   }
 }
 
+// The panel's interchanges as one row gather for the columns outside it:
+// after the swaps, row pos[i] holds what row src[i] held (rows relative to k0;
+// at most 2 jb rows move).  rec[0] = count, rec[1..] = pos, rec[1 + 2 LU_NB..]
+// = src.  One thread.
+__device__ inline void lu_record_interchanges(int* rec, const int* piv_loc, int jb) {
+  int pos[2 * LU_NB], src[2 * LU_NB];
+  int cnt = 0;
+  for (int j = 0; j < jb; ++j) {
+    pos[cnt] = j;
+    src[cnt] = j;
+    ++cnt;
+  }
+  for (int j = 0; j < jb; ++j) {
+    const int pj = piv_loc[j];
+    if (pj == j) continue;
+    int a = -1, b = -1;
+    for (int t = 0; t < cnt; ++t) {
+      if (pos[t] == j) a = t;
+      if (pos[t] == pj) b = t;
+    }
+    if (b < 0) {                     // first time row pj moves
+      pos[cnt] = pj;
+      src[cnt] = pj;
+      b = cnt++;
+    }
+    const int t = src[a];
+    src[a] = src[b];
+    src[b] = t;
+  }
+  rec[0] = cnt;
+  for (int t = 0; t < cnt; ++t) {
+    rec[1 + t] = pos[t];
+    rec[1 + 2 * LU_NB + t] = src[t];
+  }
+}
+
 // The panel step of k_getrf_panel with the panel (rows k0..n-1 of the 32 panel
 // columns) staged in shared memory: pivot search, interchanges, scaling and the
 // rank-1 updates run on-chip; afterwards the panel is written back and the rows
@@ -330,38 +366,134 @@ __global__ void __launch_bounds__(512) k_getrf_panel_smem(const MatRef<T>* mats,
   // the panel's interchanges as one row gather for the columns outside it:
   // after the swaps, row pos[i] holds what row src[i] held (rows relative to
   // k0; at most 2 jb rows move).  Applied by k_getrf_swap_trsm.
-  if (threadIdx.x == 0) {
-    int pos[2 * LU_NB], src[2 * LU_NB];
-    int cnt = 0;
-    for (int j = 0; j < jb; ++j) {
-      pos[cnt] = j;
-      src[cnt] = j;
-      ++cnt;
-    }
-    for (int j = 0; j < jb; ++j) {
-      const int pj = piv_loc[j];
-      if (pj == j) continue;
-      int a = -1, b = -1;
-      for (int t = 0; t < cnt; ++t) {
-        if (pos[t] == j) a = t;
-        if (pos[t] == pj) b = t;
-      }
-      if (b < 0) {                     // first time row pj moves
-        pos[cnt] = pj;
-        src[cnt] = pj;
-        b = cnt++;
-      }
-      const int t = src[a];
-      src[a] = src[b];
-      src[b] = t;
-    }
-    int* rec = M.aff + (size_t)b * (1 + 4 * LU_NB);
-    rec[0] = cnt;
-    for (int t = 0; t < cnt; ++t) {
-      rec[1 + t] = pos[t];
-      rec[1 + 2 * LU_NB + t] = src[t];
-    }
+  if (threadIdx.x == 0) lu_record_interchanges(M.aff + (size_t)b * (1 + 4 * LU_NB), piv_loc, jb);
+}
+
+// The panel step with the panel's rows spread over the CTAs of a thread-block
+// cluster: CTA `rank` holds panel rows [rank R, rank R + R) (R = ceil(m / C),
+// m = n - k0) in its shared memory.  For tall panels, or too few matrices to
+// fill the GPU with one CTA each.  Per column j:
+//  * every CTA publishes its best candidate (largest |value| in column j among
+//    its rows >= j, lowest row on ties) with the candidate row's panel values
+//    into every CTA's shared memory, and the owner of row j publishes row j;
+//  * one cluster barrier; every CTA then picks the same pivot row p, the owners
+//    of rows j and p write the interchanged rows from the published copies, and
+//    every CTA applies the rank-1 update to its rows below j with the pivot row
+//    (now row j), tracking the next column's candidate.
+// Same pivots and arithmetic as k_getrf_panel_smem, and the same interchange
+// record for k_getrf_swap_trsm.  The published copies are double-buffered by
+// the parity of j: a CTA writes column j+2's copies only after the barrier of
+// column j+1, which every CTA reaches after it has read column j's.
+constexpr int LU_CL_MAX = 16;
+template <typename T>
+__host__ __device__ constexpr size_t lu_cl_smem(int R) {
+  return ((size_t)R * LU_NB + (size_t)2 * (LU_CL_MAX + 1) * LU_NB) * sizeof(T);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_getrf_panel_cl(const MatRef<T>* mats, int nmat, int k0, int* flags) {
+  namespace cg = cooperative_groups;
+  extern __shared__ unsigned char lu_smem[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  __shared__ T cand_v[2][LU_CL_MAX];
+  __shared__ int cand_i[2][LU_CL_MAX];
+  __shared__ T sv[32];
+  __shared__ int si[32];
+  __shared__ int piv_loc[LU_NB];
+  const int b = blockIdx.x / C;                 // one cluster per matrix (uniform exits below)
+  if (b >= nmat) return;
+  const MatRef<T> M = mats[b];
+  const int n = M.n;
+  if (k0 >= n) return;
+  T* A = M.A;
+  const size_t ld = n;
+  const int jb = min(LU_NB, n - k0), m = n - k0;
+  const int R = (m + C - 1) / C;
+  T* P = reinterpret_cast<T*>(lu_smem);         // my rows, column-major R x jb (ld R)
+  T* pub = P + (size_t)R * LU_NB;               // [2][LU_CL_MAX + 1][LU_NB] published rows
+  const int r0 = rank * R, nr = max(0, min(R, m - r0));
+  const int tid = threadIdx.x, bd = blockDim.x;
+  for (int idx = tid; idx < nr * jb; idx += bd) {
+    const int r = idx % nr, c = idx / nr;
+    P[r + c * R] = A[(k0 + r0 + r) + (size_t)(k0 + c) * ld];
   }
+  __syncthreads();
+  T best = -1;
+  int bi = m;
+  for (int r = tid; r < nr; r += bd) {
+    T a = fabs(P[r]);
+    if (a != a) a = (T)INFINITY;
+    argmax_pair(best, bi, a, r0 + r);
+  }
+  block_argmax(best, bi, sv, si);
+  for (int j = 0; j < jb; ++j) {
+    const int par = j & 1;
+    T* slot = pub + (size_t)par * (LU_CL_MAX + 1) * LU_NB;
+    // publish my candidate (and row j if it is mine) into every CTA
+    for (int t = tid; t < C * jb; t += bd) {
+      const int d = t / jb, c = t % jb;
+      *cl.map_shared_rank(slot + (size_t)rank * LU_NB + c, d) = (bi < m) ? P[(bi - r0) + c * R] : (T)0;
+    }
+    if (tid < C) {
+      *cl.map_shared_rank(&cand_v[par][rank], tid) = best;
+      *cl.map_shared_rank(&cand_i[par][rank], tid) = bi;
+    }
+    if (j / R == rank)
+      for (int t = tid; t < C * jb; t += bd) {
+        const int d = t / jb, c = t % jb;
+        *cl.map_shared_rank(slot + (size_t)LU_CL_MAX * LU_NB + c, d) = P[(j - r0) + c * R];
+      }
+    cl.sync();
+    T bv = -1;
+    int p = m, pc = 0;
+    for (int q = 0; q < C; ++q) {
+      const T v2 = cand_v[par][q];
+      const int i2 = cand_i[par][q];
+      if (v2 > bv || (v2 == bv && i2 < p)) {
+        bv = v2;
+        p = i2;
+        pc = q;
+      }
+    }
+    if (rank == 0 && tid == 0) {
+      M.ipiv[k0 + j] = k0 + p;
+      piv_loc[j] = p;
+    }
+    const T* urow = slot + (size_t)pc * LU_NB;           // old row p: the new row j
+    const T* jrow = slot + (size_t)LU_CL_MAX * LU_NB;    // old row j
+    if (p != j && tid < jb) {
+      if (j / R == rank) P[(j - r0) + tid * R] = urow[tid];
+      if (p / R == rank) P[(p - r0) + tid * R] = jrow[tid];
+    }
+    __syncthreads();
+    const T pv = urow[j];
+    const bool bad = !(pv == pv) || isinf(pv) || pv == (T)0;
+    if (rank == 0 && tid == 0 && bad) atomicOr(flags, (pv == (T)0) ? 1 : 2);
+    best = -1;
+    bi = m;
+    for (int r = tid; r < nr; r += bd) {
+      const int i = r0 + r;
+      if (i <= j) continue;
+      if (!bad) {
+        const T l = P[r + j * R] / pv;
+        P[r + j * R] = l;
+        for (int c = j + 1; c < jb; ++c) P[r + c * R] -= l * urow[c];
+      }
+      if (j + 1 < jb) {
+        T a = fabs(P[r + (j + 1) * R]);
+        if (a != a) a = (T)INFINITY;
+        argmax_pair(best, bi, a, i);
+      }
+    }
+    block_argmax(best, bi, sv, si);
+  }
+  for (int idx = tid; idx < nr * jb; idx += bd) {
+    const int r = idx % nr, c = idx / nr;
+    A[(k0 + r0 + r) + (size_t)(k0 + c) * ld] = P[r + c * R];
+  }
+  if (rank == 0 && tid == 0) lu_record_interchanges(M.aff + (size_t)b * (1 + 4 * LU_NB), piv_loc, jb);
+  cl.sync();                                    // no CTA leaves while a peer may still address it
 }
 
 // The columns outside the panel of every matrix: apply the panel's row

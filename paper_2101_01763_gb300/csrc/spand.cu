@@ -726,6 +726,21 @@ static int launch_qrcp_stream(DevMem& tmp, const std::vector<QrStreamTask<T>>& t
   return SPAND_OK;
 }
 
+// LU panel kernel choice: SPAND_LU_PANEL=smem never uses the cluster kernel,
+// SPAND_LU_PANEL=cluster uses it for every panel taller than LU_CL_ROWS rows
+// (a checking aid: the same factorization by the other code path)
+static int lu_panel_mode() {   // 0: automatic, 1: smem, 2: cluster
+  static const int m = [] {
+    const char* v = std::getenv("SPAND_LU_PANEL");
+    if (v && std::strcmp(v, "smem") == 0) return 1;
+    if (v && std::strcmp(v, "cluster") == 0) return 2;
+    return 0;
+  }();
+  return m;
+}
+constexpr int LU_CL_FEW = 48;    // fewer active matrices than this: clusters
+constexpr int LU_CL_ROWS = 256;  // panel rows per cluster CTA aimed at
+
 // blocked getrf of every matrix, in place; pivots + permutations
 template <typename T>
 static void batched_getrf(DevMem& tmp, std::vector<MatRef<T>>& mats, int* d_flags, cudaStream_t st) {
@@ -739,11 +754,30 @@ static void batched_getrf(DevMem& tmp, std::vector<MatRef<T>>& mats, int* d_flag
   // the staged kernel's interchange records need one slot per matrix
   int* aff = tmp.alloc<int>(mats.size() * (1 + 4 * LU_NB));
   if (tmp.err) return;
+  int* aff_cl = tmp.alloc<int>(mats.size() * (1 + 4 * LU_NB));
+  if (tmp.err) return;
   static std::atomic<uint64_t> attr{0};
   once_per_device(attr, [] {
     set_dyn_smem((const void*)k_getrf_panel_smem<T>, LU_SMEM_BYTES);
+    set_dyn_smem((const void*)k_getrf_panel_cl<T>, LU_SMEM_BYTES);
     set_dyn_smem((const void*)k_ipiv_to_perm<T>, 200 * 1024);
   });
+  // the panel's row interchanges and U12 on the columns outside it, 32 columns
+  // per CTA, for the matrices of one panel launch (their records in aff order)
+  auto swap_trsm = [&](const std::vector<MatRef<T>>& list, const MatRef<T>* dlist, int k0, int tcol) {
+    std::vector<LuColTile> tl;
+    for (int b = 0; b < (int)list.size(); ++b) {
+      const int nb = list[b].n;
+      if (k0 >= nb) continue;
+      const int outside = nb - std::min(LU_NB, nb - k0);
+      for (int c0 = 0; c0 < outside; c0 += 32) tl.push_back({b, c0});
+    }
+    if (tl.empty()) return;
+    auto* dtl = tmp.upload(tl);
+    if (tmp.err) return;
+    note_launch();
+    k_getrf_swap_trsm<T><<<(unsigned)tl.size(), 256, 0, st>>>(dlist, dtl, k0, tcol);
+  };
   // Two-level blocking (the arrangement of LAPACK's blocked getrf): panels of
   // LU_NB columns are grouped in blocks of LU_NB2.  Inside a block a panel's
   // row interchanges reach every column, but its TRSM and its rank-LU_NB
@@ -754,11 +788,36 @@ static void batched_getrf(DevMem& tmp, std::vector<MatRef<T>>& mats, int* d_flag
   for (int k0 = 0; k0 < nmax; k0 += LU_NB) {
     const int K0 = k0 / LU_NB2 * LU_NB2;
     const int tcol = K0 + LU_NB2;            // TRSM / updates inside the block only
+    // panel kernels: one CTA per matrix with the panel in shared memory when
+    // there are enough matrices to fill the GPU and the panel fits; a cluster
+    // of C CTAs per matrix (the panel's rows spread over their shared memory)
+    // when the matrices are few or the panel is too tall for one CTA; the
+    // global-memory kernel beyond the clusters' capacity
+    int nact = 0;
+    for (auto& m : mats) nact += k0 < m.n;
     std::vector<MatRef<T>> small, large;
+    std::vector<std::vector<MatRef<T>>> clus(3);    // by cluster size 2 << q: 2, 4, 8
     int nsmall_max = 0;
+    std::array<int, 3> ncl_max{0, 0, 0};
     for (auto m : mats) {
       if (k0 >= m.n) continue;
-      if ((size_t)(m.n - k0) * LU_NB * sizeof(T) <= (size_t)LU_SMEM_BYTES) {
+      const int rows = m.n - k0;
+      const bool fits1 = (size_t)rows * LU_NB * sizeof(T) <= (size_t)LU_SMEM_BYTES;
+      int q = -1;
+      if (lu_panel_mode() != 1 && (!fits1 || nact < LU_CL_FEW || lu_panel_mode() == 2) && rows > LU_CL_ROWS) {
+        for (q = 0; q < 3; ++q) {                    // smallest portable cluster with <= LU_CL_ROWS rows per CTA
+          const int C = 2 << q;
+          if ((rows + C - 1) / C <= LU_CL_ROWS) break;
+        }
+        if (q == 3) q = 2;                           // 8 CTAs, more rows each
+        const int C = 2 << q;
+        if (lu_cl_smem<T>((rows + C - 1) / C) > (size_t)LU_SMEM_BYTES) q = -1;
+      }
+      if (q >= 0) {
+        m.aff = aff_cl;
+        clus[q].push_back(m);
+        ncl_max[q] = std::max(ncl_max[q], rows);
+      } else if (fits1) {
         m.aff = aff;
         small.push_back(m);
         nsmall_max = std::max(nsmall_max, m.n);
@@ -773,20 +832,32 @@ static void batched_getrf(DevMem& tmp, std::vector<MatRef<T>>& mats, int* d_flag
       const size_t sm = (size_t)(nsmall_max - k0) * std::min(LU_NB, nsmall_max - k0) * sizeof(T);
       note_launch();
       k_getrf_panel_smem<T><<<(unsigned)small.size(), 512, sm, st>>>(ds, (int)small.size(), k0, d_flags);
-      // the panel's interchanges and U12 on the columns outside it, 32 columns per CTA
-      std::vector<LuColTile> tl;
-      for (int b = 0; b < (int)small.size(); ++b) {
-        const int nb = small[b].n;
-        if (k0 >= nb) continue;
-        const int outside = nb - std::min(LU_NB, nb - k0);
-        for (int c0 = 0; c0 < outside; c0 += 32) tl.push_back({b, c0});
+      swap_trsm(small, ds, k0, tcol);
+    }
+    for (int q = 0; q < 3; ++q) {
+      if (clus[q].empty()) continue;
+      const int C = 2 << q;
+      auto* dc = tmp.upload(clus[q]);
+      if (tmp.err) return;
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = C;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3((unsigned)(clus[q].size() * C), 1, 1);
+      cfg.blockDim = dim3(256, 1, 1);
+      cfg.dynamicSmemBytes = lu_cl_smem<T>((ncl_max[q] + C - 1) / C);
+      cfg.stream = st;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      note_launch();
+      if (cudaLaunchKernelEx(&cfg, k_getrf_panel_cl<T>, (const MatRef<T>*)dc, (int)clus[q].size(), k0, d_flags) !=
+          cudaSuccess) {
+        tmp.err = 1;
+        return;
       }
-      if (!tl.empty()) {
-        auto* dtl = tmp.upload(tl);
-        if (tmp.err) return;
-        note_launch();
-        k_getrf_swap_trsm<T><<<(unsigned)tl.size(), 256, 0, st>>>(ds, dtl, k0, tcol);
-      }
+      swap_trsm(clus[q], dc, k0, tcol);
     }
     if (dlg) {
       note_launch();

@@ -377,3 +377,47 @@ def test_group_barrier_timeout_is_reported(sg):
     d = json.loads(r.stdout.split("RESULT", 1)[1])
     assert d["first"] == -7, d
     assert d["sum_r"] == d["oracle_r"] and d["apply_err"] <= 1e-9, d
+
+
+_LU_PANEL_CHILD = r"""
+import sys, json
+import numpy as np, torch
+sys.path.insert(0, {root!r})
+import paper_2101_01763_gb300 as sg
+from oracle import dg
+from synth import get_config, modal_state, naca_ogrid
+out = {{}}
+for name in ("C1", "C2"):
+    c = get_config(name)
+    X = naca_ogrid(c.n_theta, c.n_r, c.seed)
+    u = modal_state(X, c.p, c.mach, c.alpha_deg, c.amp, c.seed)
+    rhs_o, bsr, _ = dg.assemble(X, c.p, u, c.mach, c.alpha_deg, c.cfl)
+    A = sg.BSR.from_host(*bsr)
+    for prec in ("fp64", "mixed"):
+        F = sg.Factor(sg.Plan(c.n_theta, c.n_r, c.B, c.nd_depth), A, c.eps, prec)
+        out[name + prec] = F.apply(torch.as_tensor(rhs_o, device="cuda")).cpu().numpy().tolist()
+        F.close()
+print("RESULT" + json.dumps(out))
+"""
+
+
+def test_cluster_lu_panel_same_factor(sg):
+    """The LU panel kernel with the panel's rows spread over a thread-block
+    cluster (SPAND_LU_PANEL=cluster, every panel taller than 256 rows) takes the
+    same pivots and the same arithmetic as the one-CTA shared-memory panel
+    (SPAND_LU_PANEL=smem): with the GEMM kernel fixed, the two factorizations'
+    applies agree bit for bit at C1 and C2 in both precisions."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = {}
+    for mode in ("smem", "cluster"):
+        env = dict(os.environ, SPAND_LU_PANEL=mode, SPAND_GEMM="umma")
+        r = subprocess.run([sys.executable, "-c", _LU_PANEL_CHILD.format(root=root)], env=env,
+                           capture_output=True, text=True, timeout=900)
+        assert r.returncode == 0, r.stderr[-3000:]
+        res[mode] = json.loads(r.stdout.split("RESULT", 1)[1])
+    for key, z in res["smem"].items():
+        assert np.array_equal(np.asarray(z), np.asarray(res["cluster"][key])), key
