@@ -382,8 +382,8 @@ __device__ bool qrs_task(const QrStreamTask<T>& tk, int q, int G, int Gx, T* pro
     __syncthreads();
     T prt = 0;
     for (int i = k + 1 + tid; i < n; i += QRS_THREADS) prt += v[i] * v[i];
+    const T alpha = v[k];                   // read before the barriers: thread 0 rewrites v[k] below
     const T sigma = block_sum(prt, red_v);
-    const T alpha = v[k];
     T tau = 2, scale = 0;                   // column already reduced: H = I - 2 e_k e_k^T
     if (sigma > (T)0) {
       const T beta = -copysign(sqrt(alpha * alpha + sigma), alpha);
