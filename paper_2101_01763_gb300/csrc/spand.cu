@@ -1152,18 +1152,64 @@ __global__ void k_perm_slots(const PermSlotTask* tasks) {
   for (int i = threadIdx.x; i < tk.n; i += blockDim.x) tk.out[i] = tk.slots[tk.perm[i]];
 }
 
+// The level-0 gather with the pattern checks on the device (no copy of the
+// pattern to the host, no synchronisation): one CTA per BSR block k of one
+// system; its row e by binary search of row_ptr, its target cluster pair by
+// binary search of the arena's sorted pair keys (a nc + b).  A pattern the plan
+// does not describe (row pointers out of range, a column outside the system,
+// a pair absent from the level-0 pattern) sets flags[0] |= 32 and copies
+// nothing for that block; the factorization then returns SPAND_ERR_ARG.
 template <typename T>
-__global__ void k_level0_gather(const double* val, const int* row_of, const int* col, const int* cl_of,
-                                const int* pos_in, const int* loc_row_ld, T* const* dst, int nnzb, int B) {
-  // one CTA per BSR block; dst[k] = block origin, ld from the row cluster
+__global__ void k_level0_gather_dev(const double* val, const int* rp, const int* col, int Kq, int nnzb, int e0,
+                                    int B, const int* cl_of, const int* pos_in, const int* ncl,
+                                    const long long* keys, const unsigned long long* offs, int npairs, int nc,
+                                    T* arena, int* flags) {
+  __shared__ unsigned long long s_off;
+  __shared__ int s_ld, s_ok;
   const int k = blockIdx.x;
   if (k >= nnzb) return;
-  T* d = dst[k];
-  const int ld = loc_row_ld[k];
-  const double* s = val + (size_t)k * B * B;
+  if (threadIdx.x == 0) {
+    int ok = rp[0] == 0 && rp[Kq] == nnzb;
+    int lo = 0, hi = Kq;                      // the e with rp[e] <= k < rp[e + 1]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (rp[mid] <= k) lo = mid;
+      else hi = mid;
+    }
+    const int e = lo;
+    ok = ok && rp[e] <= k && k < rp[e + 1];
+    const int f = ok ? col[k] : 0;
+    ok = ok && f >= 0 && f < Kq;
+    unsigned long long off = 0;
+    int ld = 0;
+    if (ok) {
+      const int a = cl_of[e0 + e], b = cl_of[e0 + f];
+      const long long key = (long long)a * nc + b;
+      int l2 = 0, h2 = npairs;
+      while (l2 < h2) {
+        const int m = (l2 + h2) >> 1;
+        if (keys[m] < key) l2 = m + 1;
+        else h2 = m;
+      }
+      ok = l2 < npairs && keys[l2] == key;
+      if (ok) {
+        ld = ncl[a];
+        off = offs[l2] + (unsigned long long)pos_in[e0 + e] * B + (unsigned long long)pos_in[e0 + f] * B * ld;
+      }
+    }
+    if (!ok) atomicOr(flags, 32);
+    s_ok = ok;
+    s_off = off;
+    s_ld = ld;
+  }
+  __syncthreads();
+  if (!s_ok) return;
+  T* d = arena + s_off;
+  const int ld = s_ld;
+  const double* src = val + (size_t)k * B * B;
   for (int idx = threadIdx.x; idx < B * B; idx += blockDim.x) {
     const int r = idx % B, c = idx / B;
-    d[r + (size_t)c * ld] = (T)s[idx];
+    d[r + (size_t)c * ld] = (T)src[idx];
   }
 }
 
@@ -1259,37 +1305,36 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
   lvmem.st = st;
   lvmem.stage = &stage;
   SPAND_TRY(layout(P.lv[0], n, lvmem));
-  for (int q = 0; q < nsys; ++q) {
-    // gather the BSR blocks of system q into the level-0 cluster blocks
-    const bsr_matrix* A = As[q];
-    const int Kq = sysK(q), Bq = sysB(q), e0 = sysE0(q);
+  {
+    // gather every system's BSR blocks into the level-0 cluster blocks (pattern
+    // checked on the device, see k_level0_gather_dev)
     DevMem tmp;
     tmp.st = st;
     tmp.stage = &stage;
-    std::vector<int> rp(Kq + 1), col(A->nnzb);
-    SPAND_CUDA_TRY(cudaMemcpyAsync(rp.data(), A->row_ptr, sizeof(int) * (Kq + 1), cudaMemcpyDeviceToHost, st));
-    SPAND_CUDA_TRY(cudaMemcpyAsync(col.data(), A->col, sizeof(int) * A->nnzb, cudaMemcpyDeviceToHost, st));
-    SPAND_CUDA_TRY(sync_st());
-    if (rp[0] != 0 || rp[Kq] != A->nnzb) return SPAND_ERR_ARG;
-    std::vector<T*> dst(A->nnzb);
-    std::vector<int> ldv(A->nnzb);
-    for (int e = 0; e < Kq; ++e)
-      for (int k = rp[e]; k < rp[e + 1]; ++k) {
-        if (k < 0 || k >= A->nnzb || col[k] < 0 || col[k] >= Kq) return SPAND_ERR_ARG;
-        const int f = col[k];
-        const int a = cl_of[e0 + e], b = cl_of[e0 + f];
-        auto it = boff.find({a, b});
-        if (it == boff.end()) return SPAND_ERR_ARG;
-        dst[k] = arena + it->second + (size_t)pos_in[e0 + e] * Bq + (size_t)pos_in[e0 + f] * Bq * n[a];
-        ldv[k] = n[a];
-      }
-    if (A->nnzb == 0) continue;
-    T* const* d_dst = tmp.upload(dst);
-    const int* d_ld = tmp.upload(ldv);
+    std::vector<long long> keys;
+    std::vector<unsigned long long> offs;
+    keys.reserve(boff.size());
+    offs.reserve(boff.size());
+    const int nc0 = (int)n.size();
+    for (auto& kv : boff) {                   // std::map order: (a, b) ascending, so a nc + b ascending
+      keys.push_back((long long)kv.first.first * nc0 + kv.first.second);
+      offs.push_back((unsigned long long)kv.second);
+    }
+    const long long* d_keys = tmp.upload(keys);
+    const unsigned long long* d_offs = tmp.upload(offs);
+    const int* d_cl = tmp.upload(cl_of);
+    const int* d_pos = tmp.upload(pos_in);
+    const int* d_n = tmp.upload(n);
     if (tmp.err) return SPAND_ERR_NOMEM;
-    note_launch();
-    k_level0_gather<T><<<A->nnzb, 256, 0, st>>>(A->val, nullptr, nullptr, nullptr, nullptr, d_ld, d_dst, A->nnzb, Bq);
-    SPAND_CUDA_TRY(cudaGetLastError());
+    for (int q = 0; q < nsys; ++q) {
+      const bsr_matrix* A = As[q];
+      if (A->nnzb == 0) continue;
+      note_launch();
+      k_level0_gather_dev<T><<<A->nnzb, 256, 0, st>>>(A->val, A->row_ptr, A->col, sysK(q), A->nnzb, sysE0(q),
+                                                      sysB(q), d_cl, d_pos, d_n, d_keys, d_offs, (int)keys.size(),
+                                                      nc0, arena, d_flags);
+      SPAND_CUDA_TRY(cudaGetLastError());
+    }
     tmp.free_all();
   }
 
@@ -1977,6 +2022,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
     SPAND_CUDA_TRY(sync_st());
     mark(4);
     tick("e sync after RRQR");
+    if (hflags[0] & 32) return SPAND_ERR_ARG;          // a matrix pattern the plan does not describe
     if (hflags[0] & 1) return SPAND_ERR_ZERO_PIVOT;   // the root cause when both are set
     if (hflags[0] & 2) return SPAND_ERR_NONFINITE;
     if (hflags[0] & 16) {
@@ -2186,6 +2232,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
     SPAND_CUDA_TRY(cudaMemcpyAsync(hflags, d_flags, sizeof(hflags), cudaMemcpyDeviceToHost, st));
     SPAND_CUDA_TRY(sync_st());
     S.t_elim_gemm_ms += ev_read(ev_gm[D]);
+    if (hflags[0] & 32) return SPAND_ERR_ARG;
     if (hflags[0] & 1) return SPAND_ERR_ZERO_PIVOT;   // the root cause when both are set
     if (hflags[0] & 2) return SPAND_ERR_NONFINITE;
     if (std::is_same<T, float>::value && gemm_mode() != 2) {
