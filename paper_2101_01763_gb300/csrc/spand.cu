@@ -1240,14 +1240,25 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
 
   // SPAND_DEBUG=2: host time between named points of the level loop, summed
   // over levels and printed at the end (where the host, not the GPU, is busy)
+  // (with the GPU time between the same points from events on the stream: a
+  // segment whose GPU time is close to its host time kept the GPU waiting)
   std::map<std::string, double> host_ticks;
+  std::vector<std::pair<const char*, cudaEvent_t>> tick_ev;
+  std::vector<int> tick_lv;                 // level of each event (SPAND_DEBUG=3 prints per level)
+  int tick_level = 0;
   double t_tick = t_begin;
   auto tick = [&](const char* what) {
     if (debug_level() < 2) return;
     const double t = now_ms();
     host_ticks[what] += t - t_tick;
     t_tick = t;
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) == cudaSuccess && cudaEventRecord(e, st) == cudaSuccess) {
+      tick_ev.push_back({what, e});
+      tick_lv.push_back(tick_level);
+    }
   };
+  tick("start");
   auto sync_st = [&]() -> cudaError_t {
     const double t0 = now_ms();
     const cudaError_t e = cudaStreamSynchronize(st);
@@ -1421,6 +1432,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
     for (auto& pr : L.pattern)
       if (pr.first != pr.second) nbr[pr.first].push_back(pr.second);
     mark(0);
+    tick_level = l;
     tick("a nbr lists (and level start)");
     // ================= 1. eliminate interiors (Eq. 10)
     std::vector<int> I;
@@ -2247,7 +2259,24 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
   S.factor_flops = flops;
   if (debug_level() >= 3) GemmLog::get().print_and_clear();
   tick("l final sync");
-  for (auto& kv : host_ticks) std::fprintf(stderr, "spand: host %-46s %9.2f ms\n", kv.first.c_str(), kv.second);
+  if (!tick_ev.empty()) {
+    std::map<std::string, double> gpu_ticks;
+    cudaEventSynchronize(tick_ev.back().second);
+    for (size_t i = 1; i < tick_ev.size(); ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, tick_ev[i - 1].second, tick_ev[i].second) == cudaSuccess) {
+        gpu_ticks[tick_ev[i].first] += ms;
+        if (debug_level() >= 3)
+          std::fprintf(stderr, "spand: level %d GPU %-46s %9.2f ms\n", tick_lv[i], tick_ev[i].first, ms);
+      } else {
+        cudaGetLastError();
+      }
+    }
+    for (auto& te : tick_ev) cudaEventDestroy(te.second);
+    for (auto& kv : host_ticks)
+      std::fprintf(stderr, "spand: host %-46s %9.2f ms   GPU %9.2f ms\n", kv.first.c_str(), kv.second,
+                   gpu_ticks[kv.first]);
+  }
 
   mark(6);
   // ================= apply program
