@@ -1171,12 +1171,12 @@ struct OwnedScratch {
   int alloc(const GmresSizes& zs, int64_t N, cudaStream_t s) {
     st = s;
     sc.timed = true;
-    if (cudaMallocAsync(&sc.small, zs.small_tot * sizeof(double), st) != cudaSuccess ||
-        cudaMallocAsync(&sc.vec, zs.nvec * N * sizeof(double), st) != cudaSuccess ||
-        cudaMallocAsync(&sc.part, zs.part * sizeof(double), st) != cudaSuccess ||
-        cudaMallocAsync(&sc.stat, 4 * sizeof(int), st) != cudaSuccess ||
-        cudaMallocAsync((void**)&sc.dZ, zs.maxptr * sizeof(double*), st) != cudaSuccess ||
-        cudaMallocAsync((void**)&sc.dY, 64 * sizeof(double*), st) != cudaSuccess) {
+    if (pool_alloc((void**)&sc.small, zs.small_tot * sizeof(double), st) != cudaSuccess ||
+        pool_alloc((void**)&sc.vec, zs.nvec * N * sizeof(double), st) != cudaSuccess ||
+        pool_alloc((void**)&sc.part, zs.part * sizeof(double), st) != cudaSuccess ||
+        pool_alloc((void**)&sc.stat, 4 * sizeof(int), st) != cudaSuccess ||
+        pool_alloc((void**)&sc.dZ, zs.maxptr * sizeof(double*), st) != cudaSuccess ||
+        pool_alloc((void**)&sc.dY, 64 * sizeof(double*), st) != cudaSuccess) {
       cudaGetLastError();
       return SPAND_ERR_NOMEM;
     }

@@ -3,6 +3,7 @@
 #include <atomic>
 #include <cstdint>
 #include <map>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -51,6 +52,45 @@ inline void once_per_device(std::atomic<uint64_t>& done, F f) {
 // Kernel launches issued by the library since it was loaded (a CUDA-graph
 // replay adds the kernels of the graph); read by spand_kernel_launches().
 extern std::atomic<uint64_t> g_kernel_launches;
+// The library's stream-ordered memory pool (factorizations, solver scratch),
+// one per device, separate from the device's default pool: its release threshold is unbounded, so the
+// memory a factorization frees stays mapped in the pool and the next
+// factorization (and the next level of this one) reuses it instead of mapping
+// gigabytes again after every synchronisation (the default pool returns freed
+// memory to the system at each one).  The pool keeps the largest working set
+// it has served until the process ends.
+inline cudaMemPool_t factor_pool() {
+  static std::mutex mu;
+  static std::map<int, cudaMemPool_t> pools;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = pools.find(dev);
+  if (it != pools.end()) return it->second;
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool = nullptr;
+  if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+    cudaGetLastError();
+    pool = nullptr;                      // the device's default pool then
+  } else {
+    uint64_t keep = ~uint64_t(0);
+    if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) cudaGetLastError();
+  }
+  pools[dev] = pool;
+  return pool;
+}
+
+inline cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t st) {
+  cudaMemPool_t pool = factor_pool();
+  return pool ? cudaMallocFromPoolAsync(p, bytes, pool, st) : cudaMallocAsync(p, bytes, st);
+}
+
 inline void note_launch(uint64_t n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
 
 // Sets the kernel's dynamic shared-memory limit to min(want, opt-in limit of

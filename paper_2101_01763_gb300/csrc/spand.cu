@@ -13,6 +13,7 @@
 // indices), U^-1, X, Y, the scaled triangular inverses and Q_c.  The apply is
 // a fixed list of gather-GEMV launches built once per factorization.
 #include <algorithm>
+#include <stdexcept>
 #include <array>
 #include <cmath>
 #include <chrono>
@@ -159,7 +160,7 @@ struct DevMem {
     const size_t bytes = (n * sizeof(X) + 255) & ~size_t(255);
     void* p = nullptr;
     if (bytes > kSlab / 4) {
-      if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+      if (pool_alloc(&p, bytes, st) != cudaSuccess) {
         cudaGetLastError();
         err = 1;
         return nullptr;
@@ -168,7 +169,7 @@ struct DevMem {
       return static_cast<X*>(p);
     }
     if (bytes > left) {
-      if (cudaMallocAsync(&p, kSlab, st) != cudaSuccess) {
+      if (pool_alloc(&p, kSlab, st) != cudaSuccess) {
         cudaGetLastError();
         err = 1;
         return nullptr;
@@ -1152,6 +1153,21 @@ __global__ void k_perm_slots(const PermSlotTask* tasks) {
   for (int i = threadIdx.x; i < tk.n; i += blockDim.x) tk.out[i] = tk.slots[tk.perm[i]];
 }
 
+// Offsets of a level's cluster-pair blocks in its arena: keys a nc + b in
+// ascending order, looked up by binary search (a sorted array is built and
+// copied far faster than a node-based map of the same pairs).
+struct BlockIndex {
+  int nc = 0;
+  std::vector<long long> keys;
+  std::vector<unsigned long long> offs;
+  size_t at(int a, int b) const {
+    const long long k = (long long)a * nc + b;
+    const auto it = std::lower_bound(keys.begin(), keys.end(), k);
+    if (it == keys.end() || *it != k) throw std::out_of_range("cluster pair not in the level's block pattern");
+    return (size_t)offs[it - keys.begin()];
+  }
+};
+
 // The level-0 gather with the pattern checks on the device (no copy of the
 // pattern to the host, no synchronisation): one CTA per BSR block k of one
 // system; its row e by binary search of row_ptr, its target cluster pair by
@@ -1291,48 +1307,47 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
     for (int e : P.lv[0].cl[c].elems)
       for (int d = 0; d < Bq; ++d) slots[c].push_back((int)(sysDof0(q) + (int64_t)(e - sysE0(q)) * Bq + d));
   }
-  // arena of the current level: blocks in pattern U after
+  tick("a0 level-0 positions and slots");
+  // arena of the current level: blocks in pattern U after, in (a, b) order
   T* arena = nullptr;
-  std::map<std::pair<int, int>, size_t> boff;
+  BlockIndex boff;
   auto layout = [&](const LevelInfo& L, const std::vector<int>& nn, DevMem& lm) -> int {
-    boff.clear();
+    const int nc = (int)nn.size();
+    boff.nc = nc;
+    boff.keys.clear();
+    boff.keys.reserve(L.pattern.size() + L.after.size());
+    for (auto& pr : L.pattern) boff.keys.push_back((long long)pr.first * nc + pr.second);
+    for (auto& pr : L.after) boff.keys.push_back((long long)pr.first * nc + pr.second);
+    std::sort(boff.keys.begin(), boff.keys.end());
+    boff.keys.erase(std::unique(boff.keys.begin(), boff.keys.end()), boff.keys.end());
+    boff.offs.resize(boff.keys.size());
     size_t tot = 0;
-    std::vector<std::pair<int, int>> all(L.pattern);
-    all.insert(all.end(), L.after.begin(), L.after.end());
-    std::sort(all.begin(), all.end());
-    all.erase(std::unique(all.begin(), all.end()), all.end());
-    for (auto& pr : all) {
-      boff[pr] = tot;
-      tot += (size_t)nn[pr.first] * nn[pr.second];
+    for (size_t i = 0; i < boff.keys.size(); ++i) {
+      boff.offs[i] = tot;
+      tot += (size_t)nn[boff.keys[i] / nc] * nn[boff.keys[i] % nc];
     }
     arena = lm.alloc<T>(tot);
     if (lm.err) return SPAND_ERR_NOMEM;
     SPAND_CUDA_TRY(cudaMemsetAsync(arena, 0, std::max<size_t>(tot, 1) * sizeof(T), st));
     return SPAND_OK;
   };
-  auto blk = [&](int a, int b) -> T* { return arena + boff.at({a, b}); };
+  auto blk = [&](int a, int b) -> T* { return arena + boff.at(a, b); };
 
   DevMem lvmem;  // memory of the current level arena (freed after compression)
   lvmem.st = st;
   lvmem.stage = &stage;
   SPAND_TRY(layout(P.lv[0], n, lvmem));
+  tick("a1 level-0 block layout");
   {
     // gather every system's BSR blocks into the level-0 cluster blocks (pattern
     // checked on the device, see k_level0_gather_dev)
     DevMem tmp;
     tmp.st = st;
     tmp.stage = &stage;
-    std::vector<long long> keys;
-    std::vector<unsigned long long> offs;
-    keys.reserve(boff.size());
-    offs.reserve(boff.size());
+    const std::vector<long long>& keys = boff.keys;          // ascending a nc + b
     const int nc0 = (int)n.size();
-    for (auto& kv : boff) {                   // std::map order: (a, b) ascending, so a nc + b ascending
-      keys.push_back((long long)kv.first.first * nc0 + kv.first.second);
-      offs.push_back((unsigned long long)kv.second);
-    }
     const long long* d_keys = tmp.upload(keys);
-    const unsigned long long* d_offs = tmp.upload(offs);
+    const unsigned long long* d_offs = tmp.upload(boff.offs);
     const int* d_cl = tmp.upload(cl_of);
     const int* d_pos = tmp.upload(pos_in);
     const int* d_n = tmp.upload(n);
@@ -1348,6 +1363,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
     }
     tmp.free_all();
   }
+  tick("a2 level-0 gather");
 
   // phase timers (events on the factorization stream): per level RRQR and
   // elimination-GEMM start/stop; read after each level's synchronisation
@@ -1413,6 +1429,8 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
     LevelRec<T>& R = recs[l];
     R.n = n;
     R.d_slots.resize(nc);
+    tick_level = l;
+    tick("a3 level start");
     {
       // every cluster's slot list of the level in one upload
       std::vector<int> all;
@@ -1424,6 +1442,7 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
       if (pm.err) return SPAND_ERR_NOMEM;
       for (int c = 0; c < nc; ++c) R.d_slots[c] = base + off[c];
     }
+    tick("a4 slot upload");
     DevMem tmp;
     tmp.st = st;
     tmp.stage = &stage;
@@ -2194,9 +2213,9 @@ static int factor_impl(const Plan& P, const bsr_matrix* const* As, double eps, i
     lvmem2.st = st;
     lvmem2.stage = &stage;
     T* old_arena = arena;
-    std::map<std::pair<int, int>, size_t> old_off = boff;
+    const BlockIndex old_off = boff;
     SPAND_TRY(layout(L2, n2, lvmem2));
-    auto oblk = [&](int a, int b) -> T* { return old_arena + old_off.at({a, b}); };
+    auto oblk = [&](int a, int b) -> T* { return old_arena + old_off.at(a, b); };
     tick("i next-level sizes, slots, layout");
     std::vector<EyeTask<T>> eyes;
     std::vector<GemmTask<T>> t1, t2;
