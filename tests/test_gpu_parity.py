@@ -421,3 +421,52 @@ def test_cluster_lu_panel_same_factor(sg):
         res[mode] = json.loads(r.stdout.split("RESULT", 1)[1])
     for key, z in res["smem"].items():
         assert np.array_equal(np.asarray(z), np.asarray(res["cluster"][key])), key
+
+
+def test_pattern_outside_the_plan_is_rejected(sg, c1):
+    """The level-0 gather checks the matrix pattern on the device (no copy of it
+    to the host): a column index outside the system, or row pointers that do
+    not end at the block count, make the factorization return SPAND_ERR_ARG
+    (-1) without writing outside the blocks; the correct matrix then factors in
+    the same process and matches the oracle."""
+    c, rhs, A, rhs_o, bsr, S = c1
+    plan = sg.Plan(c.n_theta, c.n_r, c.B, c.nd_depth)
+    rp = A.row_ptr.cpu().numpy()
+    col = A.col.cpu().numpy()
+    col1 = col.copy()
+    col1[rp[3]] = A.K                                    # a column outside the system
+    A1 = sg.BSR(A.K, A.B, A.row_ptr, torch.as_tensor(col1, device="cuda", dtype=A.col.dtype), A.val)
+    with pytest.raises(sg.SpandError) as ei:
+        sg.Factor(plan, A1, c.eps, "mixed")
+    assert ei.value.status == -1
+    rp2 = rp.copy()
+    rp2[-1] = rp[-1] - 1                                  # row pointers that do not end at nnzb
+    A2 = sg.BSR(A.K, A.B, torch.as_tensor(rp2, device="cuda", dtype=A.row_ptr.dtype), A.col, A.val)
+    with pytest.raises(sg.SpandError) as ei:
+        sg.Factor(plan, A2, c.eps, "fp64")
+    assert ei.value.status == -1
+    F = sg.Factor(plan, A, 0.0, "fp64")
+    z = F.apply(rhs).cpu().numpy()
+    x = sla.solve(S.toarray(), rhs_o)
+    assert np.linalg.norm(z - x) <= 1e-8 * np.linalg.norm(x)
+    F.close()
+
+
+def test_repeated_factorizations_map_no_new_memory(sg):
+    """Factorizations take their device memory from the library's stream-ordered
+    pool, which keeps freed memory mapped for reuse: after the first of three
+    factorizations of the same system, the next two leave the device's free
+    memory where it was (no growth, no leak)."""
+    c = get_config("C2")
+    X = naca_ogrid(c.n_theta, c.n_r, c.seed)
+    u = modal_state(X, c.p, c.mach, c.alpha_deg, c.amp, c.seed)
+    rhs, A, _ = sg.assemble(torch.as_tensor(X, device="cuda"), c.p, torch.as_tensor(u, device="cuda"), c.mach,
+                            c.alpha_deg, c.cfl)
+    plan = sg.Plan(c.n_theta, c.n_r, c.B, c.nd_depth)
+    free = []
+    for _ in range(3):
+        F = sg.Factor(plan, A, c.eps, "mixed")
+        F.close()
+        torch.cuda.synchronize()
+        free.append(torch.cuda.mem_get_info()[0])
+    assert abs(free[2] - free[1]) <= (16 << 20) and free[1] >= free[0] - (16 << 20), free
