@@ -391,7 +391,7 @@ __host__ __device__ constexpr size_t lu_cl_smem(int R) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_getrf_panel_cl(const MatRef<T>* mats, int nmat, int k0, int* flags) {
+__global__ void __launch_bounds__(512) k_getrf_panel_cl(const MatRef<T>* mats, int nmat, int k0, int* flags) {
   namespace cg = cooperative_groups;
   extern __shared__ unsigned char lu_smem[];
   cg::cluster_group cl = cg::this_cluster();

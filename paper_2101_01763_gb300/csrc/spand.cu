@@ -847,7 +847,7 @@ static void batched_getrf(DevMem& tmp, std::vector<MatRef<T>>& mats, int* d_flag
       at[0].val.clusterDim.y = 1;
       at[0].val.clusterDim.z = 1;
       cfg.gridDim = dim3((unsigned)(clus[q].size() * C), 1, 1);
-      cfg.blockDim = dim3(256, 1, 1);
+      cfg.blockDim = dim3(512, 1, 1);
       cfg.dynamicSmemBytes = lu_cl_smem<T>((ncl_max[q] + C - 1) / C);
       cfg.stream = st;
       cfg.attrs = at;
