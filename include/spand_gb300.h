@@ -148,6 +148,13 @@ int spand_plan_export(spand_plan_t plan, int* owner, int* node_level, int* table
  * precision: SPAND_FP64 (all factor arithmetic in FP64) or SPAND_MIXED
  * (factors computed and stored in FP32 with FP32 accumulation; the outer
  * GMRES stays FP64 and acts as iterative refinement).  A is read only; the factor owns its device memory.
+ * Device memory (the factor's and the factorization's working memory, and
+ * the solvers' scratch) comes from a stream-ordered pool of the library, one
+ * per device, that keeps freed memory mapped for the next factorization or
+ * solve: after the first call the pool holds the largest working set served
+ * so far until the process ends (the device's default pool is not used).
+ * A's pattern is checked on the device against the plan (no copy to the
+ * host): a pattern the plan does not describe gives SPAND_ERR_ARG.
  * Errors: SPAND_ERR_ARG, SPAND_ERR_NOMEM, SPAND_ERR_ZERO_PIVOT,
  * SPAND_ERR_NONFINITE, SPAND_ERR_CUDA. */
 typedef struct spand_factor_s* spand_factor_t;
