@@ -48,3 +48,27 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
     monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--gpus", "2"])
     assert bench.run_reference(bench.parse()) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_prints_one_json_line(monkeypatch, capsys):
+    """Rank 0 of the reference arm (the CPU oracle on a bounded sample of the
+    headline workload) prints one JSON line with the contract's keys, the same
+    workload config as the GPU arm's, and a cpu_baseline / e2e that restate its
+    own value."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"])
+    assert bench.run_reference(bench.parse()) == 0
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["steps"] == 1 and d["warmup"] == 0
+    assert d["higher_is_better"] is False and d["value"] > 0
+    assert "256x128" in d["config"]["workload"] and d["config"]["N"] == 2097152
+    assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
