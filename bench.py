@@ -456,7 +456,8 @@ def rooflines(sg, torch, W, fst, flush, stream, peaks_):
     gm = {"kernel": "k_gemm_umma / k_gemm_tc (elimination Y, X, Schur products; 3xTF32, FP32 accumulation)",
           "bound": "tensor", "achieved": gm_ach, "peak": tf32_peak, "unit": "TFLOP/s", "frac": gm_ach / tf32_peak,
           "traffic": None, "peak_kind": f"{pk_kind} sustained bf16 x nominal tf32/bf16 ratio (1.1/2.25)",
-          "flops_per_launch": gm_fl, "ms_per_launch": gm_ms, "flops_rule": "2 m n k per product (logical)"}
+          "flops_per_launch": gm_fl, "ms_per_launch": gm_ms, "flops_rule": "useful flops: 2 m n k per full product (Schur), m n k per triangular-times-dense "
+                       "product (Y = L^-1 P^T A_sn, X = A_ns U^-1)"}
     more = [
         {"kernel": "spand_apply (k_gemv sweeps, FP32 factors)", "bound": "hbm", "achieved": app_ach,
          "peak": hbm, "unit": "GB/s", "frac": app_ach / hbm, "peak_kind": f"{pk_kind} hbm_gbs",
